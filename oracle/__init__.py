@@ -1,0 +1,226 @@
+"""FP64 CPU oracle for the RD-CNN FitzHugh-Nagumo update (arXiv 2102.10340).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import this package.
+The CUDA product path never imports, links or calls it, and the two share no
+code: this package holds its own C source (``rdcnn_oracle.c``), its own
+ctypes loader and a second, independent numpy formulation.
+
+Functions and the passages they follow:
+
+* :func:`step`, :func:`run` -- Eq. 1 with Eq. 2-3, Jacobi update, toroidal
+  boundary (Sec. II.A-II.C); plain C loops in FP64.
+* :func:`step_numpy`, :func:`run_numpy` -- the same model restated as whole-
+  array numpy code with ``np.roll`` for the periodic neighbours (the array
+  form of Sec. II.D).  A second formulation used to cross-check the C loops.
+* :func:`scalar_map` -- Eq. 1 for an isolated cell (no diffusion term).
+* :func:`adjoint` -- exact discrete adjoint of Eq. 1-3 (not in the paper;
+  derivation in ``rdcnn_oracle.c``).
+* :func:`init_state` -- u = v = k_a x (Eq. 1, first line).
+
+Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
+(fixed point, linearisation, Fourier decay, mass conservation, symmetries,
+hand-expanded tiny grids, finite differences).  None is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rdcnn_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FHN = 0
+NONE = 1
+
+# Sec. II.A: get_init_state() defaults  a=-0.3, b=1.3, eps=-0.1, c=1, Du=0.06, Dv=1, dt=0.1
+PARAM_ORDER = ("dt", "a", "b", "eps", "c", "Du", "Dv")
+
+_lock = threading.Lock()
+_default = None
+
+
+def compile_source(src_path: str, out_path: str) -> str:
+    """gcc the oracle C source into a shared object (FP contraction off, OpenMP rows)."""
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-o", tmp, src_path, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
+def build(force: bool = False) -> str:
+    """Compile ``rdcnn_oracle.c`` into ``liboracle.so`` (skipped when up to date)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    return compile_source(_SRC, _LIB)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def pvec(params: dict) -> np.ndarray:
+    """The gene + step as the 7-vector {dt, a, b, eps, c, Du, Dv} (Sec. II.B "Pars")."""
+    return np.array([float(params[k]) for k in PARAM_ORDER], dtype=np.float64)
+
+
+def _plane(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def init_state(x, ka: float = 1.0):
+    """u = v = k_a x (Eq. 1, first line)."""
+    x = _plane(x)
+    u = ka * x
+    return u.copy(), u.copy()
+
+
+class Oracle:
+    """ctypes view of one compiled copy of ``rdcnn_oracle.c``."""
+
+    FHN = FHN
+    NONE = NONE
+
+    def __init__(self, lib_path: str):
+        lib = ctypes.CDLL(lib_path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        lib.oracle_step.argtypes = [i64, i64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_step.restype = None
+        lib.oracle_run.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, i64, ctypes.c_int]
+        lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_scalar_map.argtypes = [ctypes.c_double, ctypes.c_double, dp, i64, dp, dp, dp, dp]
+        lib.oracle_scalar_map.restype = None
+        lib.oracle_adjoint.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, i64, dp, dp, i64,
+                                       dp, dp, dp, ctypes.c_int]
+        lib.oracle_adjoint.restype = ctypes.c_int
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = ctypes.c_int
+        self.lib = lib
+        self.path = lib_path
+
+    init_state = staticmethod(init_state)
+
+    def max_threads(self) -> int:
+        return int(self.lib.oracle_max_threads())
+
+    def step(self, u, v, params: dict, reaction: int = FHN, nthreads: int = 1):
+        """One Jacobi application of Eq. 1 on the whole grid (C loops, FP64)."""
+        u = _plane(u); v = _plane(v)
+        nn, nm = u.shape
+        un = np.empty_like(u); vn = np.empty_like(v)
+        p = pvec(params)
+        self.lib.oracle_step(nn, nm, _ptr(u), _ptr(v), _ptr(un), _ptr(vn), _ptr(p), reaction, nthreads)
+        return un, vn
+
+    def run(self, u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1):
+        """T applications of Eq. 1 (t = 1..T); returns new arrays (u_T, v_T)."""
+        u = _plane(u).copy(); v = _plane(v).copy()
+        if u.ndim != 2 or u.shape != v.shape:
+            raise ValueError("u and v must be 2-D planes of the same shape")
+        nn, nm = u.shape
+        p = pvec(params)
+        rc = self.lib.oracle_run(nn, nm, _ptr(u), _ptr(v), _ptr(p), reaction, int(T), nthreads)
+        if rc != 0:
+            raise RuntimeError("oracle_run failed")
+        return u, v
+
+    def scalar_map(self, u0: float, v0: float, params: dict, T: int):
+        """Trajectory of one isolated cell under Eq. 1 without diffusion; arrays of length T+1."""
+        tu = np.empty(T + 1); tv = np.empty(T + 1)
+        ou = ctypes.c_double(); ov = ctypes.c_double()
+        p = pvec(params)
+        self.lib.oracle_scalar_map(float(u0), float(v0), _ptr(p), int(T), _ptr(tu), _ptr(tv),
+                                   ctypes.byref(ou), ctypes.byref(ov))
+        return tu, tv
+
+    def adjoint(self, u0, v0, params: dict, T: int, lu_T, lv_T, n_checkpoints: int = 0,
+                reaction: int = FHN, nthreads: int = 1):
+        """Reverse-mode derivative of T steps of Eq. 1 (derivation in rdcnn_oracle.c).
+
+        Returns (dL/du0, dL/dv0, grad) with grad = dL/d[Du, Dv, a, b, eps, c], given the
+        co-state (lu_T, lv_T) = dL/d(u_T, v_T).
+        """
+        u0 = _plane(u0); v0 = _plane(v0); lu_T = _plane(lu_T); lv_T = _plane(lv_T)
+        nn, nm = u0.shape
+        lu0 = np.empty_like(u0); lv0 = np.empty_like(v0); g = np.zeros(6)
+        p = pvec(params)
+        rc = self.lib.oracle_adjoint(nn, nm, _ptr(u0), _ptr(v0), _ptr(p), reaction, int(T), _ptr(lu_T),
+                                     _ptr(lv_T), int(n_checkpoints), _ptr(lu0), _ptr(lv0), _ptr(g),
+                                     nthreads)
+        if rc != 0:
+            raise RuntimeError("oracle_adjoint failed")
+        return lu0, lv0, g
+
+    def step_numpy(self, u, v, params: dict, reaction: int = FHN):
+        return step_numpy(u, v, params, reaction)
+
+    def run_numpy(self, u, v, params: dict, T: int, reaction: int = FHN):
+        return run_numpy(u, v, params, T, reaction)
+
+
+def _get() -> Oracle:
+    global _default
+    with _lock:
+        if _default is None:
+            build()
+            _default = Oracle(_LIB)
+        return _default
+
+
+def max_threads() -> int:
+    return _get().max_threads()
+
+
+def step(u, v, params: dict, reaction: int = FHN, nthreads: int = 1):
+    return _get().step(u, v, params, reaction, nthreads)
+
+
+def run(u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1):
+    return _get().run(u, v, params, T, reaction, nthreads)
+
+
+def scalar_map(u0: float, v0: float, params: dict, T: int):
+    return _get().scalar_map(u0, v0, params, T)
+
+
+def adjoint(u0, v0, params: dict, T: int, lu_T, lv_T, n_checkpoints: int = 0,
+            reaction: int = FHN, nthreads: int = 1):
+    return _get().adjoint(u0, v0, params, T, lu_T, lv_T, n_checkpoints, reaction, nthreads)
+
+
+# ---------------------------------------------------------------------------
+# Second formulation: whole-array numpy (Sec. II.D style, np.roll neighbours).
+# Written independently of the C loops above; used only as a cross-check.
+# ---------------------------------------------------------------------------
+
+def _lap_roll(f: np.ndarray) -> np.ndarray:
+    north = np.roll(f, 1, axis=0)    # value at row i-1
+    south = np.roll(f, -1, axis=0)   # value at row i+1
+    west = np.roll(f, 1, axis=1)     # value at column j-1
+    east = np.roll(f, -1, axis=1)    # value at column j+1
+    return north + south + west + east - 4.0 * f
+
+
+def step_numpy(u, v, params: dict, reaction: int = FHN):
+    u = _plane(u); v = _plane(v)
+    dt, a, b, eps, c, Du, Dv = pvec(params)
+    if reaction == FHN:
+        f1 = c * u - u ** 3 / 3.0 - v
+        f2 = -eps * (u - b * v + a)
+    else:
+        f1 = np.zeros_like(u); f2 = np.zeros_like(v)
+    return u + dt * (f1 + Du * _lap_roll(u)), v + dt * (f2 + Dv * _lap_roll(v))
+
+
+def run_numpy(u, v, params: dict, T: int, reaction: int = FHN):
+    for _ in range(int(T)):
+        u, v = step_numpy(u, v, params, reaction)
+    return _plane(u), _plane(v)

@@ -1,0 +1,82 @@
+"""The oracle pins must catch plausible mistakes.
+
+Each case below plants one mistake in a copy of ``oracle/rdcnn_oracle.c``
+(on the CPU, in a temporary directory), compiles it, and runs every pin of
+``test_oracle_pins.py`` against the mutant.  At least one pin must fail.
+"""
+import inspect
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "rdcnn_oracle.c")
+
+MUTANTS = {
+    "cubic_over_2": ("(u * u * u) / 3.0", "(u * u * u) / 2.0"),
+    "f1_plus_v": ("- (u * u * u) / 3.0 - v;", "- (u * u * u) / 3.0 + v;"),
+    "quadratic_f1": ("p[P_C] * u - (u * u * u) / 3.0 - v", "u * (p[P_C] - u * p[P_EPS]) - v"),
+    "f2_minus_a": ("p[P_B] * v + p[P_A]", "p[P_B] * v - p[P_A]"),
+    "f2_sign": ("return -p[P_EPS] * (u", "return p[P_EPS] * (u"),
+    "lap_centre_3": ("- 4.0 * f[i * nm + j]", "- 3.0 * f[i * nm + j]"),
+    "lap_north_twice": ("im = wrap_index(i - 1, nn)", "im = wrap_index(i + 1, nn)"),
+    "lap_no_col_wrap": ("jp = wrap_index(j + 1, nm)", "jp = (j + 1 < nm ? j + 1 : j)"),
+    "du_dv_swapped": ("uc + dt * (r1 + Du * lu)", "uc + dt * (r1 + Dv * lu)"),
+    "gauss_seidel": ("r2 = reaction_f2(uc, vc, p);", "r2 = reaction_f2(uc + dt * r1, vc, p);"),
+    "dt_squared": ("vn[c] = vc + dt * (r2", "vn[c] = vc + dt * dt * (r2"),
+    "adj_jac_uu": ("ru = (c - uk * uk) * luk", "ru = (c - 3.0 * uk * uk) * luk"),
+    "adj_eps_sign": ("- eps * lvk;", "+ eps * lvk;"),
+    "adj_grad_b": ("g[3] += lvk * (eps * vk);", "g[3] += lvk * vk;"),
+    "adj_grad_du_uses_v": ("g[0] += luk * laplacian(u,", "g[0] += luk * laplacian(v,"),
+    "adj_dv_term": ("rv + Dv * laplacian(lv", "rv + Du * laplacian(lv"),
+}
+
+
+def _pin_cases():
+    cases = []
+    for name, fn in inspect.getmembers(pins, inspect.isfunction):
+        if not name.startswith("test_"):
+            continue
+        marks = getattr(fn, "pytestmark", [])
+        params = [m for m in marks if m.name == "parametrize"]
+        if not params:
+            cases.append((fn, {}))
+            continue
+        argnames, values = params[0].args[0], params[0].args[1]
+        names = [a.strip() for a in argnames.split(",")]
+        for val in values:
+            val = val if len(names) > 1 else (val,)
+            cases.append((fn, dict(zip(names, val))))
+    return cases
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_pins_reject_mutant(mutant, mutant_dir):
+    before, after = MUTANTS[mutant]
+    text = open(SRC).read()
+    assert text.count(before) >= 1, f"mutation site for {mutant} not found"
+    src = mutant_dir / f"{mutant}.c"
+    src.write_text(text.replace(before, after, 1))
+    lib = str(mutant_dir / f"{mutant}.so")
+    oracle.compile_source(str(src), lib)
+    bad = oracle.Oracle(lib)
+    caught = []
+    for fn, kwargs in _pin_cases():
+        if "oracle_mod" not in inspect.signature(fn).parameters:
+            continue
+        try:
+            fn(oracle_mod=bad, **kwargs)
+        except (AssertionError, RuntimeError, ValueError):
+            caught.append(fn.__name__)
+    assert caught, f"no pin caught mutant {mutant}"

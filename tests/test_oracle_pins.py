@@ -1,0 +1,326 @@
+"""Pins for the FP64 oracle against what the model itself fixes.
+
+Nothing here compares the oracle with itself: every check is a closed form,
+an invariant, an independent formulation or a hand-expanded neighbour list,
+chosen so that a dropped term, a wrong sign, a wrong index or a transposed
+axis in the oracle fails at least one test.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import rdcnn_inputs as inp
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# A second gene with no special values, so that terms cannot cancel by accident.
+ODD_GENE = {"dt": 0.05, "a": 0.2, "b": 0.7, "eps": 0.3, "c": 0.5, "Du": 0.11, "Dv": 0.37}
+
+
+def homogeneous_equilibrium(p):
+    """Real solutions of f1 = f2 = 0 (Eq. 2-3) for a uniform field.
+
+    f2 = 0  =>  v = (u + a) / b;  f1 = 0  =>  -u^3/3 + (c - 1/b) u - a/b = 0.
+    """
+    roots = np.roots([-1.0 / 3.0, 0.0, p["c"] - 1.0 / p["b"], -p["a"] / p["b"]])
+    real = sorted(r.real for r in roots if abs(r.imag) < 1e-12)
+    return [(u, (u + p["a"]) / p["b"]) for u in real]
+
+
+def jacobian(p, u):
+    """d(f1, f2)/d(u, v) at (u, v), differentiated from Eq. 2-3 by hand."""
+    return np.array([[p["c"] - u * u, -1.0], [-p["eps"], p["eps"] * p["b"]]])
+
+
+@pytest.mark.parametrize("gene", [inp.default_params(), ODD_GENE], ids=["default", "odd"])
+def test_fixed_point_is_stationary(oracle_mod, gene):
+    eqs = homogeneous_equilibrium(gene)
+    assert eqs, "the cubic always has a real root"
+    for us, vs in eqs:
+        u = np.full((5, 7), us)
+        v = np.full((5, 7), vs)
+        ut, vt = oracle_mod.run(u, v, gene, 400)
+        assert np.max(np.abs(ut - us)) < 1e-12
+        assert np.max(np.abs(vt - vs)) < 1e-12
+
+
+def test_default_equilibrium_value():
+    # Derived from Eq. 2-3 with the Sec. II.A defaults (a=-0.3, b=1.3, c=1): a single real
+    # equilibrium near (1.139998, 0.646153), a stable focus.
+    (us, vs), = homogeneous_equilibrium(inp.default_params())
+    assert abs(us - 1.139998) < 1e-6 and abs(vs - 0.646153) < 1e-6
+    ev = np.linalg.eigvals(jacobian(inp.default_params(), us))
+    assert np.all(ev.real < 0) and np.all(np.abs(ev.imag) > 0.3)
+
+
+@pytest.mark.parametrize("gene", [inp.default_params(), ODD_GENE], ids=["default", "odd"])
+def test_linearisation_about_equilibrium(oracle_mod, gene):
+    """A small uniform perturbation evolves by (I + dt J)^t to first order.
+
+    Pins dt and all four partial derivatives of the reaction (Eq. 2-3).
+    """
+    us, vs = homogeneous_equilibrium(gene)[-1]
+    d0 = np.array([1e-7, -0.6e-7])
+    u = np.full((3, 4), us + d0[0])
+    v = np.full((3, 4), vs + d0[1])
+    T = 60
+    ut, vt = oracle_mod.run(u, v, gene, T)
+    M = np.eye(2) + gene["dt"] * jacobian(gene, us)
+    pred = np.linalg.matrix_power(M, T) @ d0
+    got = np.array([ut[1, 2] - us, vt[1, 2] - vs])
+    assert np.linalg.norm(got - pred) <= 1e-5 * np.linalg.norm(pred) + 1e-15
+
+
+@pytest.mark.parametrize("shape,p,q", [((12, 20), 1, 3), ((16, 16), 2, 5), ((9, 7), 4, 1)])
+def test_fourier_mode_decay(oracle_mod, shape, p, q):
+    """Pure diffusion: a Fourier mode decays by 1 - dt D (4 - 2 cos kx - 2 cos ky) per step."""
+    nn, nm = shape
+    par = dict(ODD_GENE)
+    u0 = inp.fourier_mode(nn, nm, p, q)
+    v0 = inp.fourier_mode(nn, nm, q % nn, p % nm)
+    T = 25
+    ut, vt = oracle_mod.run(u0, v0, par, T, reaction=oracle_mod.NONE)
+
+    def gain(D, pp, qq):
+        return 1.0 - par["dt"] * D * (4.0 - 2.0 * np.cos(2 * np.pi * pp / nn) - 2.0 * np.cos(2 * np.pi * qq / nm))
+
+    np.testing.assert_allclose(ut, gain(par["Du"], p, q) ** T * u0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(vt, gain(par["Dv"], q % nn, p % nm) ** T * v0, rtol=0, atol=1e-12)
+
+
+def test_mass_conserved_without_reaction(oracle_mod):
+    x = inp.uniform_field(3, 13, 17)
+    y = inp.uniform_field(4, 13, 17)
+    ut, vt = oracle_mod.run(x, y, ODD_GENE, 40, reaction=oracle_mod.NONE)
+    assert abs(ut.sum() - x.sum()) < 1e-11
+    assert abs(vt.sum() - y.sum()) < 1e-11
+
+
+def test_uniform_stays_uniform_and_follows_cell_map(oracle_mod):
+    gene = inp.default_params()
+    u = np.full((6, 9), 0.37)
+    v = np.full((6, 9), -0.21)
+    ut, vt = oracle_mod.run(u, v, gene, 300)
+    assert np.all(ut == ut[0, 0]) and np.all(vt == vt[0, 0])
+    su, sv = oracle_mod.scalar_map(0.37, -0.21, gene, 300)
+    assert ut[0, 0] == su[-1] and vt[0, 0] == sv[-1]
+
+
+def test_no_diffusion_means_independent_cells(oracle_mod):
+    gene = inp.default_params(Du=0.0, Dv=0.0)
+    x = inp.uniform_field(0, 5, 6)
+    u, v = oracle_mod.init_state(x, 1.0)
+    ut, vt = oracle_mod.run(u, v, gene, 100)
+    for i in range(5):
+        for j in range(6):
+            su, sv = oracle_mod.scalar_map(x[i, j], x[i, j], gene, 100)
+            assert ut[i, j] == su[-1] and vt[i, j] == sv[-1]
+
+
+def test_one_by_one_grid_is_the_cell_map(oracle_mod):
+    """On a 1 x 1 torus every neighbour is the cell itself: the Laplacian is exactly 0."""
+    gene = inp.default_params()
+    ut, vt = oracle_mod.run(np.array([[0.8]]), np.array([[-0.4]]), gene, 200)
+    su, sv = oracle_mod.scalar_map(0.8, -0.4, gene, 200)
+    assert ut[0, 0] == su[-1] and vt[0, 0] == sv[-1]
+
+
+def test_scalar_map_closed_form_special_case(oracle_mod):
+    """With c = 0, v = 0, eps = 0 the cell map is u <- u - dt u^3 / 3, v fixed.
+
+    For a single step from u0 that is u0 (1 - dt u0^2 / 3); check against this
+    and against the known monotone decay toward 0 for |u0| < sqrt(3/dt).
+    """
+    p = {"dt": 0.1, "a": 0.0, "b": 1.0, "eps": 0.0, "c": 0.0, "Du": 0.0, "Dv": 0.0}
+    tu, tv = oracle_mod.scalar_map(1.5, 0.0, p, 50)
+    assert abs(tu[1] - 1.5 * (1 - 0.1 * 1.5 ** 2 / 3.0)) < 1e-15
+    assert np.all(np.diff(tu) < 0) and np.all(tu > 0) and np.all(tv == 0.0)
+
+
+# Neighbour lists written out by hand (N, S, W, E) for small tori, cell = (row, col).
+HAND_NEIGHBOURS = {
+    (2, 2): {
+        (0, 0): [(1, 0), (1, 0), (0, 1), (0, 1)],
+        (0, 1): [(1, 1), (1, 1), (0, 0), (0, 0)],
+        (1, 0): [(0, 0), (0, 0), (1, 1), (1, 1)],
+        (1, 1): [(0, 1), (0, 1), (1, 0), (1, 0)],
+    },
+    (2, 3): {
+        (0, 0): [(1, 0), (1, 0), (0, 2), (0, 1)],
+        (0, 1): [(1, 1), (1, 1), (0, 0), (0, 2)],
+        (0, 2): [(1, 2), (1, 2), (0, 1), (0, 0)],
+        (1, 0): [(0, 0), (0, 0), (1, 2), (1, 1)],
+        (1, 1): [(0, 1), (0, 1), (1, 0), (1, 2)],
+        (1, 2): [(0, 2), (0, 2), (1, 1), (1, 0)],
+    },
+    (3, 3): {
+        (0, 0): [(2, 0), (1, 0), (0, 2), (0, 1)],
+        (0, 1): [(2, 1), (1, 1), (0, 0), (0, 2)],
+        (0, 2): [(2, 2), (1, 2), (0, 1), (0, 0)],
+        (1, 0): [(0, 0), (2, 0), (1, 2), (1, 1)],
+        (1, 1): [(0, 1), (2, 1), (1, 0), (1, 2)],
+        (1, 2): [(0, 2), (2, 2), (1, 1), (1, 0)],
+        (2, 0): [(1, 0), (0, 0), (2, 2), (2, 1)],
+        (2, 1): [(1, 1), (0, 1), (2, 0), (2, 2)],
+        (2, 2): [(1, 2), (0, 2), (2, 1), (2, 0)],
+    },
+    (3, 4): {
+        (0, 0): [(2, 0), (1, 0), (0, 3), (0, 1)],
+        (0, 1): [(2, 1), (1, 1), (0, 0), (0, 2)],
+        (0, 2): [(2, 2), (1, 2), (0, 1), (0, 3)],
+        (0, 3): [(2, 3), (1, 3), (0, 2), (0, 0)],
+        (1, 0): [(0, 0), (2, 0), (1, 3), (1, 1)],
+        (1, 1): [(0, 1), (2, 1), (1, 0), (1, 2)],
+        (1, 2): [(0, 2), (2, 2), (1, 1), (1, 3)],
+        (1, 3): [(0, 3), (2, 3), (1, 2), (1, 0)],
+        (2, 0): [(1, 0), (0, 0), (2, 3), (2, 1)],
+        (2, 1): [(1, 1), (0, 1), (2, 0), (2, 2)],
+        (2, 2): [(1, 2), (0, 2), (2, 1), (2, 3)],
+        (2, 3): [(1, 3), (0, 3), (2, 2), (2, 0)],
+    },
+}
+
+
+@pytest.mark.parametrize("shape", sorted(HAND_NEIGHBOURS))
+def test_tiny_grids_hand_expanded(oracle_mod, shape):
+    nb = HAND_NEIGHBOURS[shape]
+    gene = ODD_GENE
+    u = inp.uniform_field(11, *shape)
+    v = inp.uniform_field(12, *shape)
+    un, vn = oracle_mod.step(u, v, gene)
+    dt, a, b, eps, c, Du, Dv = (gene[k] for k in ("dt", "a", "b", "eps", "c", "Du", "Dv"))
+    for cell, nbrs in nb.items():
+        lu = sum(u[r] for r in nbrs) - 4 * u[cell]
+        lv = sum(v[r] for r in nbrs) - 4 * v[cell]
+        eu = u[cell] + dt * (c * u[cell] - u[cell] ** 3 / 3 - v[cell] + Du * lu)
+        ev = v[cell] + dt * (-eps * (u[cell] - b * v[cell] + a) + Dv * lv)
+        assert abs(un[cell] - eu) < 1e-14 and abs(vn[cell] - ev) < 1e-14
+
+
+def test_c_loops_agree_with_numpy_formulation(oracle_mod):
+    gene = inp.default_params()
+    x = inp.uniform_field(0, 17, 23)
+    u, v = oracle_mod.init_state(x, 1.0)
+    uc, vc = oracle_mod.run(u, v, gene, 60)
+    un, vn = oracle_mod.run_numpy(u, v, gene, 60)
+    assert np.linalg.norm(uc - un) <= 1e-13 * np.linalg.norm(un)
+    assert np.linalg.norm(vc - vn) <= 1e-13 * np.linalg.norm(vn)
+
+
+def test_threads_do_not_change_results(oracle_mod):
+    x = inp.uniform_field(5, 33, 20)
+    u1, v1 = oracle_mod.run(x, x, inp.default_params(), 20, nthreads=1)
+    u4, v4 = oracle_mod.run(x, x, inp.default_params(), 20, nthreads=4)
+    assert np.array_equal(u1, u4) and np.array_equal(v1, v4)
+
+
+def test_shift_and_d4_symmetry_bitwise(oracle_mod):
+    gene = inp.default_params()
+    x = inp.uniform_field(7, 16, 16)
+    u, v = oracle_mod.run(x, -x, gene, 30)
+    us, vs = oracle_mod.run(np.roll(x, (3, -5), (0, 1)), np.roll(-x, (3, -5), (0, 1)), gene, 30)
+    assert np.array_equal(us, np.roll(u, (3, -5), (0, 1))) and np.array_equal(vs, np.roll(v, (3, -5), (0, 1)))
+    ut, vt = oracle_mod.run(x.T, -x.T, gene, 30)
+    assert np.array_equal(ut, u.T) and np.array_equal(vt, v.T)
+    uf, vf = oracle_mod.run(x[::-1, :], -x[::-1, :], gene, 30)
+    assert np.array_equal(uf, u[::-1, :]) and np.array_equal(vf, v[::-1, :])
+    ug, vg = oracle_mod.run(x[:, ::-1], -x[:, ::-1], gene, 30)
+    assert np.array_equal(ug, u[:, ::-1]) and np.array_equal(vg, v[:, ::-1])
+
+
+def test_light_cone_embedding(oracle_mod):
+    """A centred patch evolves identically on any torus large enough to hold its light cone;
+    outside the cone every cell follows the cell map started from (0, 0)."""
+    gene = inp.default_params()
+    T = 12
+    small = inp.mid_patch(0, 48, 48)
+    big = inp.mid_patch(0, 80, 80)
+    us, vs = oracle_mod.run(small, small, gene, T)
+    ub, vb = oracle_mod.run(big, big, gene, T)
+    off = 16  # patch origin moves from 16 to 32
+    assert np.array_equal(ub[off:off + 48, off:off + 48], us)
+    assert np.array_equal(vb[off:off + 48, off:off + 48], vs)
+    bu, bv = oracle_mod.scalar_map(0.0, 0.0, gene, T)
+    r0, c0 = inp.patch_origin(80, 80)
+    far = np.ones((80, 80), bool)
+    far[r0 - T:r0 + 16 + T, c0 - T:c0 + 16 + T] = False
+    assert np.all(ub[far] == bu[-1]) and np.all(vb[far] == bv[-1])
+
+
+def test_zero_steps_is_identity(oracle_mod):
+    x = inp.uniform_field(1, 4, 5)
+    u, v = oracle_mod.run(x, 2 * x, inp.default_params(), 0)
+    assert np.array_equal(u, x) and np.array_equal(v, 2 * x)
+
+
+def test_golden_small_run(oracle_mod):
+    """Regression fixture written by tests/golden/make_golden.py (oracle only)."""
+    with open(os.path.join(GOLDEN, "oracle_4x5_T10.json")) as f:
+        g = json.load(f)
+    x = inp.uniform_field(g["seed"], 4, 5)
+    u, v = oracle_mod.run(x, x, g["params"], g["T"])
+    np.testing.assert_allclose(u, np.array(g["u"]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(v, np.array(g["v"]), rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- adjoint pins
+
+def _loss(u, v, wu, wv):
+    return float(np.sum(wu * u) + np.sum(wv * v))
+
+
+@pytest.mark.parametrize("gene", [inp.default_params(), ODD_GENE], ids=["default", "odd"])
+def test_adjoint_matches_central_differences(oracle_mod, gene):
+    """Linear loss L = <wu, u_T> + <wv, v_T>; FD in every gene entry and along random directions."""
+    nn, nm, T = 7, 9, 25
+    x = inp.uniform_field(21, nn, nm)
+    y = inp.uniform_field(22, nn, nm)
+    wu = inp.uniform_field(23, nn, nm)
+    wv = inp.uniform_field(24, nn, nm)
+    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=4)
+    names = ["Du", "Dv", "a", "b", "eps", "c"]
+    for k, name in enumerate(names):
+        h = 1e-5 * max(1.0, abs(gene[name]))
+        pp = dict(gene); pp[name] += h
+        pm = dict(gene); pm[name] -= h
+        fd = (_loss(*oracle_mod.run(x, y, pp, T), wu, wv) - _loss(*oracle_mod.run(x, y, pm, T), wu, wv)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-7 * max(1.0, abs(fd)), (name, g[k], fd)
+    du = inp.uniform_field(25, nn, nm)
+    dv = inp.uniform_field(26, nn, nm)
+    h = 1e-5
+    fd = (_loss(*oracle_mod.run(x + h * du, y + h * dv, gene, T), wu, wv)
+          - _loss(*oracle_mod.run(x - h * du, y - h * dv, gene, T), wu, wv)) / (2 * h)
+    ad = float(np.sum(lu0 * du) + np.sum(lv0 * dv))
+    assert abs(ad - fd) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_adjoint_checkpoint_count_does_not_matter(oracle_mod):
+    gene = inp.default_params()
+    x = inp.uniform_field(31, 6, 8)
+    wu = inp.uniform_field(32, 6, 8)
+    ref = oracle_mod.adjoint(x, x, gene, 17, wu, 0 * wu, n_checkpoints=17)
+    for nck in (1, 3, 5, 0):
+        got = oracle_mod.adjoint(x, x, gene, 17, wu, 0 * wu, n_checkpoints=nck)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        np.testing.assert_allclose(got[2], ref[2], rtol=1e-14, atol=1e-300)
+
+
+def test_adjoint_of_pure_diffusion_is_diffusion(oracle_mod):
+    """The periodic 5-point Laplacian is symmetric, so with no reaction the adjoint sweep is
+    the forward sweep applied to the co-state, and the gene gradients of the reaction vanish."""
+    gene = ODD_GENE
+    x = inp.uniform_field(41, 8, 11)
+    wu = inp.uniform_field(42, 8, 11)
+    wv = inp.uniform_field(43, 8, 11)
+    lu0, lv0, g = oracle_mod.adjoint(x, x, gene, 13, wu, wv, reaction=oracle_mod.NONE)
+    fu, fv = oracle_mod.run(wu, wv, gene, 13, reaction=oracle_mod.NONE)
+    assert np.array_equal(lu0, fu) and np.array_equal(lv0, fv)
+    assert np.all(g[2:] == 0.0)
+
+
+def test_adjoint_zero_steps(oracle_mod):
+    x = inp.uniform_field(1, 3, 3)
+    lu0, lv0, g = oracle_mod.adjoint(x, x, inp.default_params(), 0, x, 2 * x)
+    assert np.array_equal(lu0, x) and np.array_equal(lv0, 2 * x) and np.all(g == 0)
