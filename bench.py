@@ -1,0 +1,432 @@
+"""Benchmark: cell-updates/s of the FitzHugh-Nagumo RD-CNN stepper on GB300.
+
+Headline workload ("slow growth", Sec. III.A / Table I scale): a 4096 x 4096
+FP32 torus, default gene (Sec. II.A), u = v = 0 except a seeded 16 x 16
+U[-1, 1] patch at the centre, T = 100000 steps.  One benchmark step = one
+pass of the hot path over that input: u = v = ka*x (init kernel) followed by
+T applications of Eq. 1 (AUTO variant = temporally blocked kernel).
+
+  value   device-resident input, CUDA events around K steps, cell-updates/s
+  e2e     the same through the C ABI with HOST buffers: x copied in (pinned
+          host -> device) and (u_T, v_T) read back every step
+  roofline  dominant kernel, algorithmic work per launch / measured duration
+  cpu_baseline  the FP64 CPU oracle on this host's cores, bounded sample
+  batched / adjoint  the two follow-on patterns, each against plain forward
+                     runs on the same GPU
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+Multi-GPU: the workload does not shard (one grid per GPU): N ranks run N
+independent replicas (weak scaling) and value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import rdcnn_inputs as inp  # noqa: E402
+
+N_GRID = 4096
+T_STEPS = 100_000
+PATCH = 16
+L2_BYTES = 126 * 2 ** 20
+FLOPS_PER_CELL_STEP = 27      # Eq. 1-3 as evaluated: 2 x (3 add + 1 fma) Laplacians + 7 reaction + 4 update
+BYTES_PER_CELL_STEP = 16      # FP32: read u, v; write u+, v+
+PAPER_MCELLS_4096 = 14545.0   # Table I, PyCUDA on Tesla P100-PCIE, N = 4096 (context only)
+METRIC = "Gcell-updates/s @4096^2 FP32 (frac of HBM roofline); batched & adjoint vs plain fwd"
+WORKLOAD = (f"slow-growth {N_GRID}x{N_GRID} FP32, {PATCH}x{PATCH} centre patch U[-1,1] seed 0, "
+            f"default gene, T={T_STEPS}")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "sm_max_mhz": float(pk.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm_, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm_)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample(target_s: float = 12.0, n=N_GRID):
+    """Time the FP64 oracle on a bounded sample of the headline workload (host cores)."""
+    import oracle
+
+    threads = max(1, os.cpu_count() or 1)
+    params = inp.default_params()
+    x = np.asarray(inp.mid_patch(0, n, n), dtype=np.float32).astype(np.float64)
+    u, v = oracle.init_state(x, 1.0)
+    t0 = time.perf_counter()
+    u, v = oracle.run(u, v, params, 1, nthreads=threads)
+    one = time.perf_counter() - t0
+    steps = int(max(1, min(200, target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(u, v, params, steps, nthreads=threads)
+    dt = time.perf_counter() - t0
+    rate = n * n * steps / dt / 1e9
+    return {"value": rate, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} FP64 steps of the {n}x{n} headline grid (OpenMP rows, {threads} threads), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    threads = max(1, os.cpu_count() or 1)
+    params = inp.default_params()
+    x = np.asarray(inp.mid_patch(0, N_GRID, N_GRID), dtype=np.float32).astype(np.float64)
+    # size each step to ~10 s of oracle work so K + W steps finish within minutes
+    u, v = oracle.init_state(x, 1.0)
+    t0 = time.perf_counter()
+    oracle.run(u, v, params, 1, nthreads=threads)
+    one = time.perf_counter() - t0
+    per_step = int(max(1, min(100, 10.0 / max(one, 1e-6))))
+    for _ in range(args.warmup):
+        u, v = oracle.init_state(x, 1.0)
+        oracle.run(u, v, params, per_step, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, v = oracle.init_state(x, 1.0)
+        oracle.run(u, v, params, per_step, nthreads=threads)
+    dt = time.perf_counter() - t0
+    val = N_GRID * N_GRID * per_step * args.steps / dt / 1e9
+    sample = (f"each step: init + {per_step} FP64 oracle steps of the {N_GRID}x{N_GRID} headline grid "
+              f"({threads} threads)")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_steps_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU legs
+
+def measure_launch_ms(rd, grid, variant, k, launches_per_call, reps, torch):
+    """Average duration of one kernel launch, CUDA events on the launching stream."""
+    stream = torch.cuda.current_stream()
+    T = k * launches_per_call
+    grid.run(T, variant=variant, k=k)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for s, e in ev:
+        s.record(stream)
+        grid.run(T, variant=variant, k=k)
+        e.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([s.elapsed_time(e) for s, e in ev])) / launches_per_call
+
+
+def measure_batched(rd, torch, T=5000, quick=False):
+    specs = inp.sweep_instances(0)
+    if quick:
+        specs = specs[:32]
+        T = 500
+    b = rd.Batch(specs, dtype=torch.float32)
+    xs = []
+    for i, s in enumerate(specs):
+        x = torch.from_numpy(inp.uniform_field(s["x_seed"], s["nn"], s["nm"])).float()
+        xs.append(x)
+        b.set_state(i, x, x)
+    from paper_2102_10340_gb300 import autotune
+
+    tune = autotune.tune_batch(b, trial_steps=40 if not quick else 8)
+    b.set_tune(**tune)
+    for i, x in enumerate(xs):
+        b.set_state(i, x, x)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(); b.run(T); e.record(); torch.cuda.synchronize()
+    ms_b = s.elapsed_time(e)
+    cells = b.cells()
+    # plain forward, one Grid per instance, same stream
+    grids = [rd.Grid(sp["nn"], sp["nm"], sp["params"], dtype=torch.float32) for sp in specs]
+    for g, x in zip(grids, xs):
+        g.set_state(x.cuda(), x.cuda())
+    for g in grids:
+        g.run(8)
+    torch.cuda.synchronize()
+    s.record()
+    for g in grids:
+        g.run(T)
+    e.record(); torch.cuda.synchronize()
+    ms_p = s.elapsed_time(e)
+    for g in grids:
+        g.close()
+    return {"value": cells * T / (ms_b * 1e-3) / 1e9, "unit": "Gcell-updates/s",
+            "instances": len(specs), "T": T, "cells": cells, "ms": ms_b, "tune": tune,
+            "plain_fwd_value": cells * T / (ms_p * 1e-3) / 1e9, "plain_fwd_ms": ms_p,
+            "vs_plain_fwd": ms_p / ms_b}
+
+
+def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
+    if quick:
+        T = 200
+    p = inp.default_params()
+    x = torch.from_numpy(inp.uniform_field(0, N, N)).float().cuda()
+    target = torch.from_numpy(inp.checkerboard(0, N, N)).float().cuda()
+    g = rd.Grid(N, N, p, dtype=torch.float32)
+    g.set_state(x, x).run(T)
+    uT = g.u.clone()
+    gu = (2.0 * (uT - target) / uT.numel()).contiguous()
+    gv = torch.zeros_like(gu)
+    ws = torch.empty(g.adjoint_workspace_bytes(T), dtype=torch.uint8, device="cuda")
+    g.adjoint(T, x, x, gu, gv, workspace=ws)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.adjoint(T, x, x, gu, gv, workspace=ws)
+    t_adj = time.perf_counter() - t0
+    g.set_state(x, x).run(T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_state(x, x).run(T)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    return {"grid": [N, N], "T": T, "checkpoints": int(np.ceil(np.sqrt(T))), "adjoint_ms": t_adj * 1e3,
+            "plain_fwd_ms": t_fwd * 1e3, "adjoint_over_fwd": t_adj / t_fwd,
+            "value": N * N * T / t_adj / 1e9, "unit": "Gcell-updates/s (forward steps differentiated)"}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2102_10340_gb300 import rdcnn as rd
+
+    rd.launch_count()  # loads librdcnn.so or raises
+    N, T = args.grid, args.T
+    x_host = torch.from_numpy(np.asarray(inp.mid_patch(0, N, N), dtype=np.float32)).pin_memory()
+    x_dev = x_host.to(dev)
+    grid = rd.Grid(N, N, inp.default_params(), dtype=torch.float32, device=dev)
+    from paper_2102_10340_gb300 import autotune
+
+    if args.no_tune:
+        tune = {"variant": args.variant, "k": args.k, "rows": args.rows}
+    else:
+        tune = autotune.tune_grid(grid, x_dev, trial_steps=max(8, T // 2000))
+    grid.set_tune(k=tune["k"], rows=tune["rows"])
+    variant = tune["variant"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        grid.init(x_dev, 1.0)
+        grid.run(T, variant=variant, k=tune["k"])
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    l0 = rd.launch_count()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        step()
+    e.record()
+    barrier()
+    launches = rd.launch_count() - l0
+    clocks = sampler.stop()
+    ms = s.elapsed_time(e)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cell_steps = N * N * T * args.steps * world
+    value = cell_steps / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned): H2D x, run, D2H (u, v)
+    hu = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    hv = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    grid.init(x_host, 1.0).run(T, variant=variant, k=tune["k"])
+    grid.get_state(hu, hv)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        grid.init(x_host, 1.0)
+        grid.run(T, variant=variant, k=tune["k"])
+        grid.get_state(hu, hv)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = cell_steps / t_e2e / 1e9
+    finite = bool(torch.isfinite(torch.from_numpy(hu.numpy())).all())
+
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    peaks = load_peaks()
+    # roofline of the dominant kernel (one launch advances k steps over the whole grid)
+    k = tune["k"] if variant == "temporal" else 1
+    launch_ms = measure_launch_ms(rd, grid, variant, k, 2, 20, torch)
+    cells = N * N
+    if variant == "temporal" and k > 1:
+        flops = FLOPS_PER_CELL_STEP * cells * k
+        # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+        peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        ach = flops / (launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
+                    "traffic": None, "kernel": f"k_temporal<float,K={k}>",
+                    "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz "
+                                   f"({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})",
+                    "launch_ms": launch_ms,
+                    "hbm_equiv": {"achieved": BYTES_PER_CELL_STEP * cells / (launch_ms * 1e-3) / 1e9,
+                                  "peak": peaks["hbm_gbs"], "unit": "GB/s"}}
+    else:
+        byts = BYTES_PER_CELL_STEP * cells
+        ach = byts / (launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "k_step1<float>",
+                    "peak_source": peaks["source"], "launch_ms": launch_ms}
+    # the unfused single-step kernel against the HBM roofline (16 B per cell-step)
+    s1_ms = measure_launch_ms(rd, grid, "step1", 1, 2, 20, torch)
+    s1_gbs = BYTES_PER_CELL_STEP * cells / (s1_ms * 1e-3) / 1e9
+    step1 = {"kernel": "k_step1<float>", "launch_ms": s1_ms, "gcell_s": cells / (s1_ms * 1e-3) / 1e9,
+             "achieved_gbs": s1_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": s1_gbs / peaks["hbm_gbs"]}
+
+    extra = {}
+    if not args.no_extras:
+        extra["batched"] = measure_batched(rd, torch, quick=args.quick)
+        extra["adjoint"] = measure_adjoint(rd, torch, quick=args.quick)
+    cpu = None if args.no_cpu else oracle_sample(6.0 if args.quick else 12.0, n=N)
+
+    line = {"metric": METRIC, "value": value, "unit": "Gcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / (PAPER_MCELLS_4096 / 1000.0), "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if (N, T) == (N_GRID, T_STEPS) else f"{N}x{N} FP32 patch, T={T}",
+                       "grid": [N, N], "T": T, "variant": variant, "k": k, "rows": tune["rows"],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: 4 x 64 MiB planes (state + ping-pong) vs 126 MiB L2",
+                       "vs_baseline_ref": "Table I PyCUDA 14545 Mcell/s at N=4096, Tesla P100 (context)"},
+            "e2e": {"value": e2e_value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 4 * N * N,
+                    "d2h_bytes_per_step": 2 * 4 * N * N, "finite": finite},
+            "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
+            "single_step_kernel": step1, "cpu_baseline": cpu}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--T", type=int, default=T_STEPS)
+    ap.add_argument("--quick", action="store_true", help="small batched/adjoint/cpu legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
+    ap.add_argument("--variant", default="temporal", choices=("temporal", "step1", "generic"))
+    ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--rows", type=int, default=128)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * rdcnn.h -- C ABI of the GB300 (sm_103a) RD-CNN FitzHugh-Nagumo stepper.
+ *
+ * The library advances the two-layer reaction-diffusion cellular nonlinear
+ * network of Dogaru & Dogaru (arXiv 2102.10340), Sec. II.A, Eq. 1-3:
+ *
+ *   u+_ij = u_ij + dt [ f1(u_ij, v_ij) + Du (u_{i+1,j} + u_{i-1,j} + u_{i,j-1} + u_{i,j+1} - 4 u_ij) ]
+ *   v+_ij = v_ij + dt [ f2(u_ij, v_ij) + Dv (v_{i+1,j} + v_{i-1,j} + v_{i,j-1} + v_{i,j+1} - 4 v_ij) ]
+ *   f1(u, v) = c u - u^3 / 3 - v          (Eq. 2)
+ *   f2(u, v) = -eps (u - b v + a)         (Eq. 3)
+ *
+ * for every cell at once (both "+" values from the old state), T times, on
+ * an NN x NM torus (indices wrap on both axes, the only boundary of the
+ * paper, Sec. II.B-II.C).
+ *
+ * Conventions shared by every entry point
+ *  - Layout: one plane per field, row-major [NN][NM], element (i, j) at
+ *    offset i * NM + j; i is the row (NN rows), j the column (NM columns).
+ *  - Element type: float (RDCNN_F32) or double (RDCNN_F64), fixed per handle.
+ *  - Memory ownership: the CALLER owns every buffer, host or device.  The
+ *    library never allocates device memory; scratch space is passed in by
+ *    the caller, sized by the matching *_workspace_bytes query.
+ *  - Streams: work is enqueued on the caller's CUDA stream (cudaStream_t
+ *    passed as void*; NULL = legacy default stream).  Calls that return data
+ *    to host memory synchronise that stream before returning; all other calls
+ *    are asynchronous.
+ *  - Errors: every int-returning call returns RDCNN_OK (0), a positive
+ *    warning, or a negative error code; rdcnn_last_error() then describes the
+ *    last failure on the calling thread.  Invalid arguments are rejected on
+ *    the host before any GPU work is enqueued.
+ *  - Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef RDCNN_H
+#define RDCNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The gene plus the time step (Sec. II.A "Pars": dt, a, b, eps, c, Du, Dv).
+ * Paper defaults (Sec. II.A, get_init_state): dt=0.1, a=-0.3, b=1.3,
+ * eps=-0.1, c=1, Du=0.06, Dv=1. */
+typedef struct rdcnn_params {
+    double dt, a, b, eps, c, Du, Dv;
+} rdcnn_params;
+
+enum rdcnn_status {
+    RDCNN_OK = 0,
+    RDCNN_WARN_CFL = 1,     /* accepted, but dt * max(Du, Dv) > 1/4: the explicit
+                               5-point scheme is then not von Neumann stable */
+    RDCNN_EINVAL = -1,      /* bad argument: size, pointer, alignment, enum, non-finite param */
+    RDCNN_ECUDA = -2,       /* a CUDA runtime call or kernel launch failed */
+    RDCNN_ETIMEOUT = -3,    /* a bounded device-side wait gave up */
+    RDCNN_ENONFINITE = -4,  /* a NaN or Inf was found where a finite value is required */
+    RDCNN_ESTATE = -5,      /* handle not bound to state buffers */
+    RDCNN_ESPACE = -6       /* caller-provided workspace is too small */
+};
+
+enum { RDCNN_BC_PERIODIC = 0 };                   /* toroidal wrap, Sec. II.B-II.C */
+enum { RDCNN_F32 = 0, RDCNN_F64 = 1 };
+enum { RDCNN_REACTION_FHN = 0,                    /* Eq. 2-3 */
+       RDCNN_REACTION_NONE = 1 };                 /* f1 = f2 = 0: pure diffusion (testing) */
+enum { RDCNN_VARIANT_AUTO = 0,                    /* library's choice (temporal when possible) */
+       RDCNN_VARIANT_STEP1 = 1,                   /* one launch per time step, float4/double2 rows */
+       RDCNN_VARIANT_TEMPORAL = 2,                /* k time steps fused per launch */
+       RDCNN_VARIANT_GENERIC = 3 };               /* scalar path: any size, any alignment */
+
+/* Launch shape: k = time steps fused per launch of the temporal kernels
+ * (1..8 F32, 1..4 F64; 0 = library default), rows = grid rows each warp
+ * walks (0 = library default).  Neither changes results, only speed. */
+typedef struct rdcnn_tune {
+    int k;
+    int rows;
+} rdcnn_tune;
+
+typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
+
+/* ------------------------------------------------------------------ single grid */
+
+/* Create a handle for an NN x NM grid (Sec. II.A: "NNxNM" array of cells).
+ * nn, nm >= 1; p finite; boundary = RDCNN_BC_PERIODIC; dtype RDCNN_F32/F64;
+ * reaction RDCNN_REACTION_FHN/NONE.  Pure host call (no CUDA work).
+ * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL. */
+int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p,
+                 int boundary, int dtype, int reaction);
+
+/* Replace the gene of an existing handle (same validation as create). */
+int rdcnn_set_params(rdcnn_t *h, const rdcnn_params *p);
+
+/* Set the handle's launch shape (see rdcnn_tune); NULL restores defaults.
+ * rdcnn_run uses tune->k when its own k argument is 0, and tune->rows for
+ * the rows per warp of every vectorised variant.  Errors: RDCNN_EINVAL. */
+int rdcnn_set_tune(rdcnn_t *h, const rdcnn_tune *tune);
+
+/* Bytes of device scratch rdcnn_run needs: two planes (the "Anew"/"Bnew"
+ * ping-pong partners of Sec. II.B), NN * NM * sizeof(element) each. */
+int rdcnn_workspace_bytes(const rdcnn_t *h, size_t *bytes);
+
+/* Attach caller-owned device buffers: u and v planes (the state, updated in
+ * place by rdcnn_run), scratch of at least rdcnn_workspace_bytes, and the
+ * stream all later work is enqueued on.  Pointers must be device pointers;
+ * 16-byte alignment enables the vectorised kernels (otherwise the generic
+ * path is used).  Errors: RDCNN_EINVAL (null pointer), RDCNN_ESPACE. */
+int rdcnn_bind(rdcnn_t *h, void *u, void *v, void *workspace, size_t workspace_bytes,
+               void *stream);
+
+/* Initial state u = v = ka * x (Eq. 1, first line; Sec. II.A "scaling factor
+ * k_a").  x is an NN x NM plane of the handle's dtype, in host memory
+ * (x_on_device = 0; copied in, the call returns when x may be reused) or
+ * device memory (x_on_device = 1; asynchronous).  Errors: RDCNN_ESTATE,
+ * RDCNN_EINVAL, RDCNN_ECUDA. */
+int rdcnn_init(rdcnn_t *h, const void *x, double ka, int x_on_device);
+
+/* Load an arbitrary state (u0, v0) (checkpoint restore).  Same memory rules
+ * as rdcnn_init. */
+int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
+
+/* Apply Eq. 1 T times (t = 1..T, Sec. II.A) to the bound state, in place.
+ * variant: RDCNN_VARIANT_*; k: time steps fused per launch for the temporal
+ * variant (0 = library default; 1..8 for F32, 1..4 for F64).  T = 0 is a
+ * no-op.  Asynchronous on the bound stream.  The vectorised variants need
+ * NM to be a multiple of 4 (F32) or 2 (F64) and 16-byte aligned buffers;
+ * AUTO falls back to GENERIC otherwise, an explicit request returns
+ * RDCNN_EINVAL.  Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
+int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k);
+
+/* Copy the current state out (the "lastA, lastB" the paper's display
+ * function returns, Sec. II.A).  to_device = 0: host buffers, the call
+ * synchronises the stream; to_device = 1: device buffers, asynchronous.
+ * Either output pointer may be NULL to skip that field. */
+int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device);
+
+/* Release the handle (not the caller's buffers).  NULL is ignored. */
+void rdcnn_destroy(rdcnn_t *h);
+
+/* ------------------------------------------------------------------ batched sweep */
+
+/* One instance of a parameter sweep (Sec. III.A explores the (Du, Dv) plane
+ * and Sec. III.B the (a, b) plane by running many simulations).  Each
+ * instance has its own grid size and its own gene, dt included.
+ * u, v: the instance's state planes (device, updated in place);
+ * su, sv: two scratch planes of the same size (device). */
+typedef struct rdcnn_instance {
+    int64_t nn, nm;
+    rdcnn_params params;
+    void *u, *v;
+    void *su, *sv;
+} rdcnn_instance;
+
+/* Bytes of device workspace rdcnn_batch_run needs for its work table. */
+int rdcnn_batch_workspace_bytes(const rdcnn_instance *inst, int n, int dtype,
+                                const rdcnn_tune *tune, size_t *bytes);
+
+/* Run T steps of Eq. 1 on all n instances with the same reaction and dtype.
+ * All instances advance together: each launch covers every instance for k
+ * steps, so small grids do not pay one launch per step each.  Vectorised
+ * layout rules as for rdcnn_run apply to every instance (NM multiple of
+ * 4 / 2, 16-byte aligned pointers), else RDCNN_EINVAL.  tune may be NULL.
+ * Asynchronous on `stream`, except that the work table is copied to the
+ * device first (host-synchronous copy into `workspace`). */
+int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction,
+                    const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
+                    void *stream);
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Bytes of device workspace rdcnn_adjoint needs for T steps with
+ * n_checkpoints stored states (0 = ceil(sqrt(T))). */
+int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpoints,
+                                  size_t *bytes);
+
+/* Reverse-mode derivative of T steps of Eq. 1-3 (not in the paper: the
+ * exact discrete adjoint of the update, for gradient-based fitting of the
+ * gene the paper searches for in Sec. III).  Given the start state (u0, v0)
+ * and the co-state dL/du_T, dL/dv_T of a loss L of the final state, writes
+ * dL/du0, dL/dv0 (device planes) and grad[6] = dL/d{Du, Dv, a, b, eps, c}
+ * (host array, FP64).  Forward states are rebuilt from n_checkpoints stored
+ * states (0 = ceil(sqrt(T))).  All planes are device planes of the handle's
+ * size and dtype; the bound u/v/workspace of the handle are not touched.
+ * Synchronises the handle's stream (grad is a host result). */
+int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
+                  const void *dLdu_T, const void *dLdv_T, int64_t n_checkpoints,
+                  void *dLdu0, void *dLdv0, double grad[6],
+                  void *workspace, size_t workspace_bytes);
+
+/* ------------------------------------------------------------------ diagnostics */
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *rdcnn_last_error(void);
+
+/* Number of kernels this library has launched in this process (all devices,
+ * all handles).  Used by benchmarks to report launch counts. */
+uint64_t rdcnn_launch_count(void);
+
+/* Library version string. */
+const char *rdcnn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDCNN_H */

@@ -1,0 +1,245 @@
+// api.cu -- the C ABI of include/rdcnn.h for the single-grid calls:
+// handle life cycle, state I/O and the T-step driver (Eq. 1, t = 1..T).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "rdcnn.h"
+
+struct rdcnn {
+    int64_t nn = 0, nm = 0;
+    rdcnn_params p{};
+    int dtype = RDCNN_F32;
+    int reaction = RDCNN_REACTION_FHN;
+    void *u = nullptr, *v = nullptr, *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+    int tune_k = 0, tune_rows = 0;
+};
+
+namespace rdk {
+
+namespace {
+thread_local char g_err[512] = "";
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    return set_error(RDCNN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int check_params(const rdcnn_params *p) {
+    if (!p) return set_error(RDCNN_EINVAL, "params is NULL");
+    const double vals[7] = {p->dt, p->a, p->b, p->eps, p->c, p->Du, p->Dv};
+    for (double x : vals)
+        if (!std::isfinite(x)) return set_error(RDCNN_ENONFINITE, "non-finite gene entry");
+    if (p->Du < 0 || p->Dv < 0) return set_error(RDCNN_EINVAL, "diffusion coefficients must be >= 0");
+    const double dmax = p->Du > p->Dv ? p->Du : p->Dv;
+    if (p->dt * dmax > 0.25) {
+        set_error(RDCNN_WARN_CFL, "dt*max(Du,Dv) = %g > 1/4: explicit scheme unstable", p->dt * dmax);
+        return RDCNN_WARN_CFL;
+    }
+    return RDCNN_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
+                int *reaction, cudaStream_t *stream) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    *nn = h->nn; *nm = h->nm; *p = h->p; *dtype = h->dtype; *reaction = h->reaction;
+    *stream = h->stream;
+    return RDCNN_OK;
+}
+
+}  // namespace rdk
+
+using namespace rdk;
+
+extern "C" {
+
+const char *rdcnn_last_error(void) { return g_err; }
+
+uint64_t rdcnn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *rdcnn_version(void) { return "rdcnn 0.1 (sm_103a)"; }
+
+int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p, int boundary,
+                 int dtype, int reaction) {
+    g_err[0] = '\0';
+    if (!out) return set_error(RDCNN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nn < 1 || nm < 1) return set_error(RDCNN_EINVAL, "grid size must be >= 1 (got %lld x %lld)", (long long)nn, (long long)nm);
+    if (nn > 0x7fffffff || nm > 0x7fffffff || nn * nm > (int64_t(1) << 40))
+        return set_error(RDCNN_EINVAL, "grid too large");
+    if (boundary != RDCNN_BC_PERIODIC) return set_error(RDCNN_EINVAL, "only RDCNN_BC_PERIODIC is supported");
+    if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "dtype must be RDCNN_F32 or RDCNN_F64");
+    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE)
+        return set_error(RDCNN_EINVAL, "unknown reaction");
+    const int pc = check_params(p);
+    if (pc < 0) return pc;
+    rdcnn_t *h = new (std::nothrow) rdcnn_t();
+    if (!h) return set_error(RDCNN_EINVAL, "out of host memory");
+    h->nn = nn; h->nm = nm; h->p = *p; h->dtype = dtype; h->reaction = reaction;
+    *out = h;
+    return pc;
+}
+
+int rdcnn_set_params(rdcnn_t *h, const rdcnn_params *p) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    const int pc = check_params(p);
+    if (pc < 0) return pc;
+    h->p = *p;
+    return pc;
+}
+
+int rdcnn_set_tune(rdcnn_t *h, const rdcnn_tune *tune) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!tune) { h->tune_k = 0; h->tune_rows = 0; return RDCNN_OK; }
+    if (tune->k < 0 || tune->k > max_k(h->dtype))
+        return set_error(RDCNN_EINVAL, "k must be in 0..%d", max_k(h->dtype));
+    if (tune->rows < 0 || tune->rows > (1 << 20)) return set_error(RDCNN_EINVAL, "rows out of range");
+    h->tune_k = tune->k;
+    h->tune_rows = tune->rows;
+    return RDCNN_OK;
+}
+
+int rdcnn_workspace_bytes(const rdcnn_t *h, size_t *bytes) {
+    if (!h || !bytes) return set_error(RDCNN_EINVAL, "NULL argument");
+    *bytes = 2 * (size_t)h->nn * (size_t)h->nm * elem_size(h->dtype);
+    return RDCNN_OK;
+}
+
+int rdcnn_bind(rdcnn_t *h, void *u, void *v, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!u || !v || !workspace) return set_error(RDCNN_EINVAL, "state and workspace pointers must be non-NULL");
+    size_t need = 0;
+    rdcnn_workspace_bytes(h, &need);
+    if (workspace_bytes < need)
+        return set_error(RDCNN_ESPACE, "workspace has %zu bytes, need %zu", workspace_bytes, need);
+    h->u = u; h->v = v; h->ws = workspace; h->ws_bytes = workspace_bytes;
+    h->stream = (cudaStream_t)stream;
+    h->bound = true;
+    return RDCNN_OK;
+}
+
+int rdcnn_init(rdcnn_t *h, const void *x, double ka, int x_on_device) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
+    if (!x) return set_error(RDCNN_EINVAL, "x is NULL");
+    if (!std::isfinite(ka)) return set_error(RDCNN_ENONFINITE, "ka is not finite");
+    const int64_t n = h->nn * h->nm;
+    const size_t bytes = (size_t)n * elem_size(h->dtype);
+    cudaError_t e;
+    if (!x_on_device) {
+        e = cudaMemcpyAsync(h->u, x, bytes, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "copy x to device");
+        e = launch_init(h->dtype, h->u, h->u, h->v, ka, n, h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "init kernel");
+        e = cudaStreamSynchronize(h->stream);  // x (host) may be reused on return
+        if (e != cudaSuccess) return cuda_error(e, "init synchronize");
+    } else {
+        e = launch_init(h->dtype, x, h->u, h->v, ka, n, h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "init kernel");
+    }
+    return RDCNN_OK;
+}
+
+int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
+    if (!u0 || !v0) return set_error(RDCNN_EINVAL, "state pointer is NULL");
+    const size_t bytes = (size_t)h->nn * h->nm * elem_size(h->dtype);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(h->u, u0, bytes, kind, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->v, v0, bytes, kind, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(e, "set_state copy");
+    return RDCNN_OK;
+}
+
+int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
+    if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
+    if (variant < RDCNN_VARIANT_AUTO || variant > RDCNN_VARIANT_GENERIC)
+        return set_error(RDCNN_EINVAL, "unknown variant %d", variant);
+    if (T == 0) return RDCNN_OK;
+    const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
+    char *ws = (char *)h->ws;
+    void *su = ws, *sv = ws + plane;
+    const bool vec_ok = (h->nm % vec_width(h->dtype) == 0) && aligned16(h->u) && aligned16(h->v) &&
+                        aligned16(su) && aligned16(sv);
+    if (variant == RDCNN_VARIANT_AUTO) variant = vec_ok ? RDCNN_VARIANT_TEMPORAL : RDCNN_VARIANT_GENERIC;
+    if ((variant == RDCNN_VARIANT_STEP1 || variant == RDCNN_VARIANT_TEMPORAL) && !vec_ok)
+        return set_error(RDCNN_EINVAL,
+                         "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
+                         vec_width(h->dtype));
+    if (variant == RDCNN_VARIANT_TEMPORAL) {
+        if (k == 0) k = h->tune_k ? h->tune_k : default_k(h->dtype);
+        if (k < 1 || k > max_k(h->dtype))
+            return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(h->dtype));
+    } else {
+        k = 1;
+    }
+    const void *cu = h->u, *cv = h->v;
+    void *nu = su, *nv = sv;
+    int64_t left = T;
+    while (left > 0) {
+        const int kk = (int)(left < k ? left : k);
+        cudaError_t e;
+        if (variant == RDCNN_VARIANT_TEMPORAL)
+            e = launch_temporal(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                                h->tune_rows ? h->tune_rows : default_rows_temporal(h->dtype, kk, h->nn, h->nm),
+                                h->stream);
+        else if (variant == RDCNN_VARIANT_STEP1)
+            e = launch_step1(h->dtype, h->reaction, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                             h->tune_rows ? h->tune_rows : default_rows_step1(h->dtype, h->nn, h->nm),
+                             h->stream);
+        else
+            e = launch_generic(h->dtype, h->reaction, cu, cv, nu, nv, h->nn, h->nm, h->p, h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "step kernel launch");
+        const void *tu = cu, *tv = cv;
+        cu = nu; cv = nv;
+        nu = const_cast<void *>(tu); nv = const_cast<void *>(tv);
+        left -= kk;
+    }
+    if (cu != h->u) {
+        cudaError_t e = cudaMemcpyAsync(h->u, cu, plane, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->v, cv, plane, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_error(e, "copy back to state");
+    }
+    return RDCNN_OK;
+}
+
+int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device) {
+    if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
+    if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
+    const size_t bytes = (size_t)h->nn * h->nm * elem_size(h->dtype);
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (u_out) e = cudaMemcpyAsync(u_out, h->u, bytes, kind, h->stream);
+    if (e == cudaSuccess && v_out) e = cudaMemcpyAsync(v_out, h->v, bytes, kind, h->stream);
+    if (e == cudaSuccess && !to_device) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_error(e, "get_state copy");
+    return RDCNN_OK;
+}
+
+void rdcnn_destroy(rdcnn_t *h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,298 @@
+// forward.cu -- forward kernels for Eq. 1-3 (Sec. II.A) on a torus.
+//
+//  k_step1     one time step per launch.  A warp owns a band of 32*V columns
+//              (V = 4 floats / 2 doubles per lane, one 16-byte load) and walks
+//              down a strip of rows, keeping rows i-1, i, i+1 in registers and
+//              prefetching row i+2.  Horizontal neighbours come from the
+//              adjacent lane by warp shuffle; the two band-edge values are
+//              read from global memory (L1/L2 hits).  Each input byte is read
+//              once from DRAM and each output byte written once: 16 B per
+//              cell-step in FP32, the algorithmic minimum.
+//  k_temporal  K time steps per launch.  A warp loads a band of 32*V columns
+//              that overlaps its neighbours by H = ceil(K/V) lanes on each
+//              side, and walks down rows r0-K .. r0+R+K-1 of its strip.  Stage
+//              s of a K-deep register pipeline turns three rows of stage s-1
+//              into one row of stage s, so a row is read once and leaves as
+//              K-step-advanced output: DRAM traffic is 16 B per cell per K
+//              steps.  Lanes within K columns of the band edge hold stale
+//              values after K steps and do not store.
+//  k_generic   one thread per cell, scalar loads: any size and alignment.
+//
+// All three evaluate cells with rdk::fhn_cell, so they produce identical
+// bits for identical inputs.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "temporal.cuh"
+
+namespace rdk {
+
+namespace {
+
+constexpr int kStep1Block = 256;
+constexpr int kTemporalBlock = 128;
+
+// --------------------------------------------------------------------------- single step
+
+template <typename T, int RX>
+__global__ void __launch_bounds__(kStep1Block)
+k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
+        T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
+    constexpr int V = Vec<T>::N;
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * (kStep1Block / 32) + (threadIdx.x >> 5);
+    if (wid >= nwarps) return;  // whole warps only
+    const int band = wid % bands;
+    const int strip = wid / bands;
+    const int col = band * 32 * V + lane * V;
+    const bool active = col < nm;
+    const int colw = (col == 0) ? nm - 1 : col - 1;
+    const int cole = (col + V >= nm) ? 0 : col + V;
+    const bool edge_w = (lane == 0);
+    const bool edge_e = active && (lane == 31 || col + V >= nm);
+    const int r0 = strip * rows;
+    const int r1 = min(r0 + rows, nn);
+
+    Slice<T> nor, cen, sou, pre;
+    T cw_u = 0, ce_u = 0, cw_v = 0, ce_v = 0;  // band-edge values of row "cen"
+    T sw_u = 0, se_u = 0, sw_v = 0, se_v = 0;  // ... of row "sou"
+    T pw_u = 0, pe_u = 0, pw_v = 0, pe_v = 0;  // ... of row "pre"
+    zero_slice(nor); zero_slice(cen); zero_slice(sou); zero_slice(pre);
+
+    int rn = (r0 == 0) ? nn - 1 : r0 - 1;
+    int rc = r0;
+    int rs = (r0 + 1 == nn) ? 0 : r0 + 1;
+    if (active) {
+        load_slice(nor, u, v, (int64_t)rn * nm + col);
+        load_slice(cen, u, v, (int64_t)rc * nm + col);
+        load_slice(sou, u, v, (int64_t)rs * nm + col);
+    }
+    if (edge_w) {
+        cw_u = __ldg(u + (int64_t)rc * nm + colw); cw_v = __ldg(v + (int64_t)rc * nm + colw);
+        sw_u = __ldg(u + (int64_t)rs * nm + colw); sw_v = __ldg(v + (int64_t)rs * nm + colw);
+    }
+    if (edge_e) {
+        ce_u = __ldg(u + (int64_t)rc * nm + cole); ce_v = __ldg(v + (int64_t)rc * nm + cole);
+        se_u = __ldg(u + (int64_t)rs * nm + cole); se_v = __ldg(v + (int64_t)rs * nm + cole);
+    }
+
+    for (int r = r0; r < r1; ++r) {
+        // prefetch row r+2 (wrapped) while row r is computed
+        const bool more = (r + 1 < r1);
+        const int rp = (rs + 1 == nn) ? 0 : rs + 1;
+        if (more) {
+            if (active) load_slice(pre, u, v, (int64_t)rp * nm + col);
+            if (edge_w) { pw_u = __ldg(u + (int64_t)rp * nm + colw); pw_v = __ldg(v + (int64_t)rp * nm + colw); }
+            if (edge_e) { pe_u = __ldg(u + (int64_t)rp * nm + cole); pe_v = __ldg(v + (int64_t)rp * nm + cole); }
+        }
+        T wu = __shfl_up_sync(kFull, cen.u[V - 1], 1);
+        T eu = __shfl_down_sync(kFull, cen.u[0], 1);
+        T wv = __shfl_up_sync(kFull, cen.v[V - 1], 1);
+        T ev = __shfl_down_sync(kFull, cen.v[0], 1);
+        if (edge_w) { wu = cw_u; wv = cw_v; }
+        if (edge_e) { eu = ce_u; ev = ce_v; }
+        Slice<T> out;
+        slice_update<T, RX>(nor, cen, sou, wu, eu, wv, ev, p, out);
+        if (active) {
+            const int64_t off = (int64_t)r * nm + col;
+            store_vec<T>(un + off, out.u);
+            store_vec<T>(vn + off, out.v);
+        }
+        nor = cen; cen = sou; sou = pre;
+        cw_u = sw_u; ce_u = se_u; cw_v = sw_v; ce_v = se_v;
+        sw_u = pw_u; se_u = pe_u; sw_v = pw_v; se_v = pe_v;
+        rs = rp;
+    }
+}
+
+// --------------------------------------------------------------------------- temporal blocking
+
+template <typename T, int K, int RX>
+__global__ void __launch_bounds__(kTemporalBlock)
+k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
+           T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
+    const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
+    if (wid >= nwarps) return;  // whole warps only
+    constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
+    temporal_strip<T, K, H, RX>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
+}
+
+// --------------------------------------------------------------------------- generic
+
+template <typename T, int RX>
+__global__ void __launch_bounds__(256)
+k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
+          T *__restrict__ vn, int nn, int nm, Coef<T> p) {
+    const int64_t n = (int64_t)nn * nm;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / nm);
+        const int j = (int)(idx - (int64_t)i * nm);
+        const int ip = (i + 1 == nn) ? 0 : i + 1;
+        const int im = (i == 0) ? nn - 1 : i - 1;
+        const int jp = (j + 1 == nm) ? 0 : j + 1;
+        const int jm = (j == 0) ? nm - 1 : j - 1;
+        const int64_t ri = (int64_t)i * nm;
+        const int64_t rp = (int64_t)ip * nm;
+        const int64_t rm = (int64_t)im * nm;
+        T ou, ov;
+        fhn_cell<T, RX>(u[ri + j], u[rm + j], u[rp + j], u[ri + jm], u[ri + jp],
+                        v[ri + j], v[rm + j], v[rp + j], v[ri + jm], v[ri + jp], p, ou, ov);
+        un[idx] = ou;
+        vn[idx] = ov;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_init(const T *__restrict__ x, T *u, T *v, T ka, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T t = mul_rn(ka, x[i]);
+        u[i] = t;
+        v[i] = t;
+    }
+}
+
+template <typename T>
+cudaError_t step1_t(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
+                    int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
+    constexpr int V = Vec<T>::N;
+    const int bands = (int)((nm + 32 * V - 1) / (32 * V));
+    const int strips = (int)((nn + rows - 1) / rows);
+    const int64_t nwarps = (int64_t)bands * strips;
+    const int wpb = kStep1Block / 32;
+    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
+    const Coef<T> c = make_coef<T>(p);
+    if (reaction == RDCNN_REACTION_FHN)
+        k_step1<T, RX_FHN><<<grid, kStep1Block, 0, s>>>((const T *)u, (const T *)v, (T *)un,
+                                                        (T *)vn, (int)nn, (int)nm, bands,
+                                                        (int)nwarps, rows, c);
+    else
+        k_step1<T, RX_NONE><<<grid, kStep1Block, 0, s>>>((const T *)u, (const T *)v, (T *)un,
+                                                         (T *)vn, (int)nn, (int)nm, bands,
+                                                         (int)nwarps, rows, c);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, int K>
+cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, void *vn,
+                        int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
+    constexpr int V = Vec<T>::N;
+    constexpr int H = (K + V - 1) / V;
+    constexpr int OUTW = (32 - 2 * H) * V;
+    const int bands = (int)((nm + OUTW - 1) / OUTW);
+    const int strips = (int)((nn + rows - 1) / rows);
+    const int64_t nwarps = (int64_t)bands * strips;
+    const int wpb = kTemporalBlock / 32;
+    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
+    const Coef<T> c = make_coef<T>(p);
+    if (reaction == RDCNN_REACTION_FHN)
+        k_temporal<T, K, RX_FHN><<<grid, kTemporalBlock, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps,
+            rows, c);
+    else
+        k_temporal<T, K, RX_NONE><<<grid, kTemporalBlock, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps,
+            rows, c);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t generic_t(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
+                      int64_t nm, const rdcnn_params &p, cudaStream_t s) {
+    const int64_t n = nn * nm;
+    const int64_t want = (n + 255) / 256;
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)sm_count() * 16);
+    const Coef<T> c = make_coef<T>(p);
+    if (reaction == RDCNN_REACTION_FHN)
+        k_generic<T, RX_FHN><<<grid, 256, 0, s>>>((const T *)u, (const T *)v, (T *)un, (T *)vn,
+                                                  (int)nn, (int)nm, c);
+    else
+        k_generic<T, RX_NONE><<<grid, 256, 0, s>>>((const T *)u, (const T *)v, (T *)un, (T *)vn,
+                                                   (int)nn, (int)nm, c);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+        return n;
+    return 152;
+}
+
+cudaError_t launch_step1(int dtype, int reaction, const void *u, const void *v, void *un,
+                         void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
+                         cudaStream_t s) {
+    if (dtype == RDCNN_F64) return step1_t<double>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+    return step1_t<float>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+}
+
+cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const void *v,
+                            void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                            int rows, cudaStream_t s) {
+    if (dtype == RDCNN_F64) {
+        switch (k) {
+            case 1: return temporal_tk<double, 1>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 2: return temporal_tk<double, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 3: return temporal_tk<double, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 4: return temporal_tk<double, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (k) {
+        case 1: return temporal_tk<float, 1>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 2: return temporal_tk<float, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 3: return temporal_tk<float, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 4: return temporal_tk<float, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 5: return temporal_tk<float, 5>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 6: return temporal_tk<float, 6>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 7: return temporal_tk<float, 7>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 8: return temporal_tk<float, 8>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v, void *un,
+                           void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                           cudaStream_t s) {
+    if (dtype == RDCNN_F64) return generic_t<double>(reaction, u, v, un, vn, nn, nm, p, s);
+    return generic_t<float>(reaction, u, v, un, vn, nn, nm, p, s);
+}
+
+cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
+                        cudaStream_t s) {
+    const int64_t want = (n + 255) / 256;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 16));
+    if (dtype == RDCNN_F64)
+        k_init<double><<<grid, 256, 0, s>>>((const double *)x, (double *)u, (double *)v, ka, n);
+    else
+        k_init<float><<<grid, 256, 0, s>>>((const float *)x, (float *)u, (float *)v, (float)ka, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int default_k(int dtype) { return dtype == RDCNN_F64 ? 4 : 8; }
+
+// Launch shapes measured on GB300 at 4096^2 FP32: the single-step kernel is
+// fastest with short strips (more warps in flight), the temporal kernel with
+// strips long enough to amortise the 2k-row pipeline fill.
+int default_rows_step1(int dtype, int64_t nn, int64_t nm) {
+    (void)dtype; (void)nn; (void)nm;
+    return 4;
+}
+
+int default_rows_temporal(int dtype, int k, int64_t nn, int64_t nm) {
+    (void)dtype; (void)nm;
+    const int r = nn >= 2048 ? 128 : (nn >= 512 ? 64 : 32);
+    return std::max(r, 4 * k);
+}
+
+}  // namespace rdk

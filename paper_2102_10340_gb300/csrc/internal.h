@@ -1,0 +1,62 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rdcnn.h"
+
+namespace rdk {
+
+// Launch-shape limits of the vectorised kernels.
+constexpr int kMaxK32 = 8;  // temporal depth, FP32
+constexpr int kMaxK64 = 4;  // temporal depth, FP64
+
+inline int vec_width(int dtype) { return dtype == RDCNN_F64 ? 2 : 4; }
+inline size_t elem_size(int dtype) { return dtype == RDCNN_F64 ? 8 : 4; }
+inline int max_k(int dtype) { return dtype == RDCNN_F64 ? kMaxK64 : kMaxK32; }
+
+// Columns of output a warp of the temporal kernel produces for depth k.
+inline int temporal_out_cols(int dtype, int k) {
+    const int V = vec_width(dtype);
+    const int H = (k + V - 1) / V;
+    return (32 - 2 * H) * V;
+}
+
+void count_launches(uint64_t n);
+
+// Error reporting (thread-local message, returned code passes through).
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+// Validates a gene: RDCNN_OK, RDCNN_WARN_CFL, or a negative code.
+int check_params(const rdcnn_params *p);
+bool aligned16(const void *p);
+int sm_count();
+
+// Read-only view of a handle's configuration (defined in api.cu); the stream
+// is the one bound by rdcnn_bind (NULL if unbound).
+int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
+                int *reaction, cudaStream_t *stream);
+
+// Kernel launchers.  All return the launch status (cudaGetLastError()).
+// u/v are read, un/vn written; the two pairs must not overlap.
+cudaError_t launch_step1(int dtype, int reaction, const void *u, const void *v, void *un,
+                         void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
+                         cudaStream_t s);
+cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const void *v,
+                            void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                            int rows, cudaStream_t s);
+cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v, void *un,
+                           void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                           cudaStream_t s);
+// u = v = ka * x; x may alias u.
+cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
+                        cudaStream_t s);
+
+// Default launch shapes (rows per warp strip) and temporal depth.
+int default_rows_step1(int dtype, int64_t nn, int64_t nm);
+int default_rows_temporal(int dtype, int k, int64_t nn, int64_t nm);
+int default_k(int dtype);
+
+}  // namespace rdk

@@ -1,0 +1,93 @@
+// temporal.cuh -- the K-step register pipeline shared by the single-grid and
+// batched temporally blocked kernels (Eq. 1 applied K times per HBM pass).
+//
+// A warp owns one (band, strip) work item: output columns
+// [band*OUTW, band*OUTW + OUTW) and output rows [strip*rows, strip*rows + rows)
+// of an NN x NM torus.  It loads 32*V columns starting H*V columns to the left
+// of its band (H = ceil(K/V) halo lanes per side, indices wrapped modulo NM)
+// and input rows r0-K .. r0+rows+K-1 (wrapped modulo NN).  Each input row
+// passes through K stages held in registers; stage s turns rows (q-1, q, q+1)
+// of stage s-1 into row q of stage s.  After K stages the K outermost columns
+// on each side are stale, which is why only lanes H .. 31-H store.
+#pragma once
+
+#include "common.cuh"
+
+namespace rdk {
+
+// One pipeline beat: consume input row m of the strip, advance every stage by
+// one row, and store the finished row (stage K) when it is inside the strip.
+// W[PH], W[PH+1] hold the two older rows of each stage, W[PH+2] receives the
+// newest, so a 3-beat unroll rotates the windows without register moves.
+template <typename T, int K, int RX, int PH>
+__device__ __forceinline__ void temporal_beat(int m, int total, Slice<T> (&W)[3][K],
+                                              Slice<T> &nxt, int &g, int nn, int nm, int lc,
+                                              const T *__restrict__ u, const T *__restrict__ v,
+                                              T *__restrict__ un, T *__restrict__ vn,
+                                              int r0, int sc, bool st_lane, const Coef<T> &p) {
+    constexpr int V = Vec<T>::N;
+    if (m >= total) return;
+    Slice<T> cur = nxt;
+    if (m + 1 < total) {
+        g = (g + 1 == nn) ? 0 : g + 1;
+        load_slice(nxt, u, v, (int64_t)g * nm + lc);
+    }
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        Slice<T> &A = W[PH][s];
+        Slice<T> &B = W[(PH + 1) % 3][s];
+        const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
+        const T eu = __shfl_down_sync(kFull, B.u[0], 1);
+        const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
+        const T ev = __shfl_down_sync(kFull, B.v[0], 1);
+        Slice<T> out;
+        slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
+        W[(PH + 2) % 3][s] = cur;
+        cur = out;
+    }
+    const int orow = m - 2 * K;
+    if (orow >= 0 && st_lane) {
+        const int64_t off = (int64_t)(r0 + orow) * nm + sc;
+        store_vec<T>(un + off, cur.u);
+        store_vec<T>(vn + off, cur.v);
+    }
+}
+
+// H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
+// needed only narrows the band), which lets a batched launch use one band
+// layout for launches of different depth.
+template <typename T, int K, int H, int RX>
+__device__ __forceinline__ void temporal_strip(int band, int strip, const T *__restrict__ u,
+                                               const T *__restrict__ v, T *__restrict__ un,
+                                               T *__restrict__ vn, int nn, int nm, int rows,
+                                               const Coef<T> &p) {
+    constexpr int V = Vec<T>::N;
+    static_assert(H * V >= K, "halo narrower than the temporal depth");
+    static_assert(2 * H < 32, "halo wider than the warp");
+    constexpr int OUTW = (32 - 2 * H) * V;
+    const int lane = threadIdx.x & 31;
+    const int c0 = band * OUTW;
+    const int lc = wrap_row((int64_t)c0 - H * V + lane * V, nm);  // V-aligned since nm % V == 0
+    const int sc = c0 + (lane - H) * V;
+    const bool st_lane = (lane >= H) && (lane < 32 - H) && (sc < nm);
+    const int r0 = strip * rows;
+    const int nout = min(rows, nn - r0);
+    const int total = nout + 2 * K;
+
+    Slice<T> W[3][K];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int s = 0; s < K; ++s) zero_slice(W[a][s]);
+
+    int g = wrap_row((int64_t)r0 - K, nn);
+    Slice<T> nxt;
+    load_slice(nxt, u, v, (int64_t)g * nm + lc);
+    for (int m = 0; m < total; m += 3) {
+        temporal_beat<T, K, RX, 0>(m, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+        temporal_beat<T, K, RX, 1>(m + 1, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+        temporal_beat<T, K, RX, 2>(m + 2, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+    }
+}
+
+}  // namespace rdk

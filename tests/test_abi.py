@@ -1,0 +1,160 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+``include/rdcnn.h`` declares, and rejects bad arguments on the host before any
+CUDA work (no compute calls are made here)."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rdcnn.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rdcnn_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2102_10340_gb300 import _lib, build_library
+
+    build_library()
+    return _lib.load()
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2102_10340_gb300 import _lib
+
+    return _lib
+
+
+def test_header_declares_expected_calls():
+    names = header_functions()
+    for must in ("rdcnn_create", "rdcnn_init", "rdcnn_run", "rdcnn_batch_run", "rdcnn_adjoint",
+                 "rdcnn_get_state", "rdcnn_destroy"):
+        assert must in names
+
+
+def test_every_header_symbol_is_exported(lib):
+    from paper_2102_10340_gb300.build import LIB
+
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (rdcnn_\w+)", out))
+    missing = [n for n in header_functions() if n not in exported]
+    assert not missing, missing
+    for n in header_functions():
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_header_exactly(L):
+    assert sorted(name for name, _, _ in L.SIGNATURES) == header_functions()
+
+
+def test_struct_layouts(L):
+    assert ctypes.sizeof(L.Params) == 7 * 8
+    assert ctypes.sizeof(L.Tune) == 8
+    assert ctypes.sizeof(L.Instance) == 2 * 8 + 7 * 8 + 4 * 8
+
+
+def _create(lib, L, nn=8, nm=8, params=None, boundary=0, dtype=0, reaction=0):
+    h = ctypes.c_void_p()
+    p = L.params_struct(params or {"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0})
+    rc = lib.rdcnn_create(ctypes.byref(h), nn, nm, ctypes.byref(p), boundary, dtype, reaction)
+    return rc, h
+
+
+def test_create_validation(lib, L):
+    assert _create(lib, L, nn=0)[0] == L.EINVAL
+    assert _create(lib, L, nm=-3)[0] == L.EINVAL
+    assert _create(lib, L, boundary=1)[0] == L.EINVAL
+    assert _create(lib, L, dtype=7)[0] == L.EINVAL
+    assert _create(lib, L, reaction=5)[0] == L.EINVAL
+    bad = {"dt": 0.1, "a": math.nan, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0}
+    assert _create(lib, L, params=bad)[0] == L.ENONFINITE
+    neg = {"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": -0.06, "Dv": 1.0}
+    assert _create(lib, L, params=neg)[0] == L.EINVAL
+    assert "diffusion" in L.last_error()
+    rc, h = _create(lib, L)
+    assert rc == L.OK and h.value
+    lib.rdcnn_destroy(h)
+    lib.rdcnn_destroy(None)
+
+
+def test_cfl_warning_still_creates(lib, L):
+    hot = {"dt": 0.3, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0}
+    rc, h = _create(lib, L, params=hot)
+    assert rc == L.WARN_CFL and h.value
+    lib.rdcnn_destroy(h)
+
+
+def test_unbound_handle_and_workspace(lib, L):
+    rc, h = _create(lib, L, nn=6, nm=10, dtype=L.F64)
+    n = ctypes.c_size_t()
+    assert lib.rdcnn_workspace_bytes(h, ctypes.byref(n)) == L.OK
+    assert n.value == 2 * 6 * 10 * 8
+    assert lib.rdcnn_run(h, 5, 0, 0) == L.ESTATE
+    assert lib.rdcnn_get_state(h, None, None, 0) == L.ESTATE
+    assert lib.rdcnn_init(h, None, 1.0, 1) == L.ESTATE
+    assert lib.rdcnn_bind(h, None, None, None, 0, None) == L.EINVAL
+    assert lib.rdcnn_bind(h, 16, 32, 48, 10, None) == L.ESPACE
+    t = L.Tune(9, 0)
+    assert lib.rdcnn_set_tune(h, ctypes.byref(t)) == L.EINVAL  # F64 allows k <= 4
+    t = L.Tune(3, 16)
+    assert lib.rdcnn_set_tune(h, ctypes.byref(t)) == L.OK
+    assert lib.rdcnn_set_tune(h, None) == L.OK
+    a = ctypes.c_size_t()
+    assert lib.rdcnn_adjoint_workspace_bytes(h, 100, 0, ctypes.byref(a)) == L.OK
+    assert a.value >= (10 + 10 + 4) * 2 * 6 * 10 * 8 // 2
+    lib.rdcnn_destroy(h)
+
+
+def test_bound_run_rejects_bad_args_before_gpu_work(lib, L):
+    rc, h = _create(lib, L, nn=4, nm=6)
+    # fake, never-dereferenced addresses: validation must fail before any CUDA call
+    assert lib.rdcnn_bind(h, 256, 512, 1024, 4 * 6 * 4 * 2, None) == L.OK
+    assert lib.rdcnn_run(h, -1, 0, 0) == L.EINVAL
+    assert lib.rdcnn_run(h, 5, 9, 0) == L.EINVAL
+    assert lib.rdcnn_run(h, 5, L.VARIANT_TEMPORAL, 0) == L.EINVAL  # NM=6 is not a multiple of 4
+    assert "multiple" in L.last_error() or "aligned" in L.last_error()
+    assert lib.rdcnn_run(h, 0, 0, 0) == L.OK  # T = 0 is a no-op
+    lib.rdcnn_destroy(h)
+
+
+def test_batch_validation(lib, L):
+    p = L.params_struct({"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0})
+    tab = (L.Instance * 2)()
+    tab[0] = L.Instance(8, 8, p, 256, 512, 768, 1024)
+    tab[1] = L.Instance(8, 6, p, 256, 512, 768, 1024)
+    n = ctypes.c_size_t()
+    assert lib.rdcnn_batch_workspace_bytes(tab, 2, 0, None, ctypes.byref(n)) == L.OK and n.value > 0
+    assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL  # NM=6
+    tab[1] = L.Instance(8, 8, p, 256, 0, 768, 1024)
+    assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL  # NULL
+    tab[1] = L.Instance(8, 8, p, 256, 520, 768, 1024)
+    assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL  # misaligned
+    tab[1] = L.Instance(8, 8, p, 256, 512, 768, 1024)
+    t = L.Tune(12, 0)
+    assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, ctypes.byref(t), 4096, n.value, None) == L.EINVAL
+    assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, 1, None) == L.ESPACE
+    assert lib.rdcnn_batch_run(tab, 0, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL
+
+
+def test_adjoint_validation(lib, L):
+    rc, h = _create(lib, L, nn=4, nm=8)
+    g = (ctypes.c_double * 6)()
+    assert lib.rdcnn_adjoint(h, 10, 256, 512, 768, 1024, 0, 1280, 1536, g, None, 0) == L.EINVAL
+    assert lib.rdcnn_adjoint(h, 10, 256, 512, 768, 1024, 0, 1280, 1540, g, 4096, 1 << 20) == L.EINVAL
+    assert lib.rdcnn_adjoint(h, 10, 256, 512, 768, 1024, 0, 1280, 1536, g, 4096, 16) == L.ESPACE
+    assert lib.rdcnn_adjoint(h, -2, 256, 512, 768, 1024, 0, 1280, 1536, g, 4096, 1 << 20) == L.EINVAL
+    lib.rdcnn_destroy(h)
+
+
+def test_version_and_counter(lib):
+    assert b"rdcnn" in lib.rdcnn_version()
+    assert lib.rdcnn_launch_count() >= 0

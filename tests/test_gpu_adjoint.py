@@ -1,0 +1,165 @@
+"""Reverse-time adjoint on the GPU vs the oracle adjoint (itself pinned to
+finite differences on the CPU), vs finite differences of the GPU forward, and
+through torch.autograd.
+
+Tolerances: FP64 kernels 1e-8..1e-10 relative (rounding order only); FP32
+kernels 1e-4 relative for the gene-gradient vector (the stated gradient
+target), with the FP64 oracle started from the same FP32-rounded state.
+"""
+import numpy as np
+import pytest
+import torch
+
+import rdcnn_inputs as inp
+from _util import cpu_threads, f32, gpu_run, normwise
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = torch.float32, torch.float64
+NAMES = ("Du", "Dv", "a", "b", "eps", "c")
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _gpu_adjoint(rd, u0, v0, params, T, gu, gv, dtype, nck=0):
+    g = rd.Grid(u0.shape[0], u0.shape[1], params, dtype=dtype)
+    du, dv, gp = g.adjoint(T, _dev(u0, dtype), _dev(v0, dtype), _dev(gu, dtype), _dev(gv, dtype), nck)
+    torch.cuda.synchronize()
+    return du.double().cpu().numpy(), dv.double().cpu().numpy(), np.array([gp[k] for k in NAMES])
+
+
+@pytest.mark.parametrize("nck", [0, 1, 7, 50])
+def test_f64_adjoint_matches_oracle(rd, oracle_mod, nck):
+    nn, nm, T = 24, 40, 50
+    params = inp.default_params()
+    x = inp.uniform_field(1, nn, nm)
+    y = inp.uniform_field(2, nn, nm)
+    wu = inp.uniform_field(3, nn, nm)
+    wv = inp.uniform_field(4, nn, nm)
+    du, dv, g = _gpu_adjoint(rd, x, y, params, T, wu, wv, F64, nck)
+    ou, ov, og = oracle_mod.adjoint(x, y, params, T, wu, wv, n_checkpoints=nck)
+    assert normwise(du, ou) < 1e-10 and normwise(dv, ov) < 1e-10
+    np.testing.assert_allclose(g, og, rtol=1e-9, atol=1e-12)
+
+
+def test_f64_adjoint_vs_gpu_finite_differences(rd):
+    nn, nm, T = 16, 32, 30
+    params = {"dt": 0.05, "a": 0.2, "b": 0.7, "eps": 0.3, "c": 0.5, "Du": 0.11, "Dv": 0.37}
+    x = inp.uniform_field(5, nn, nm)
+    y = inp.uniform_field(6, nn, nm)
+    wu = inp.uniform_field(7, nn, nm)
+    wv = inp.uniform_field(8, nn, nm)
+    _, _, g = _gpu_adjoint(rd, x, y, params, T, wu, wv, F64)
+
+    def loss(p):
+        u, v = gpu_run(rd, x, y, p, T, F64, "temporal", 3)
+        return float(np.sum(wu * u) + np.sum(wv * v))
+
+    for k, name in enumerate(NAMES):
+        h = 1e-5 * max(1.0, abs(params[name]))
+        pp = dict(params); pp[name] += h
+        pm = dict(params); pm[name] -= h
+        fd = (loss(pp) - loss(pm)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * max(1.0, abs(fd)), (name, g[k], fd)
+
+
+def test_adjoint_without_reaction_is_forward_of_costate(rd):
+    """Self-adjointness of the periodic Laplacian: with no reaction the adjoint sweep
+    equals the forward sweep applied to the co-state, bit for bit."""
+    nn, nm, T = 32, 64, 21
+    params = inp.default_params(Du=0.13, Dv=0.21)
+    x = f32(inp.uniform_field(9, nn, nm))
+    wu = f32(inp.uniform_field(10, nn, nm))
+    wv = f32(inp.uniform_field(11, nn, nm))
+    g = rd.Grid(nn, nm, params, dtype=F32, reaction="none")
+    du, dv, gp = g.adjoint(T, _dev(x, F32), _dev(x, F32), _dev(wu, F32), _dev(wv, F32))
+    fu, fv = gpu_run(rd, wu, wv, params, T, F32, "step1", reaction="none")
+    assert np.array_equal(du.double().cpu().numpy(), fu) and np.array_equal(dv.double().cpu().numpy(), fv)
+    assert all(gp[k] == 0.0 for k in ("a", "b", "eps", "c"))
+
+
+def _mse_seed(uT, target):
+    return 2.0 * (uT - target) / uT.size
+
+
+@pytest.mark.parametrize("T", [200, 2000])
+def test_f32_checkerboard_mse_512(rd, oracle_mod, T):
+    """512^2 FP32, MSE(u_T, checkerboard of period 32), sqrt(T) checkpoints.
+
+    Gene gradient: ||g_gpu - g_ref|| / ||g_ref|| <= 1e-4 against the FP64 oracle adjoint
+    (which is pinned to FP64 finite differences).  The vector norm is the measure: single
+    entries can be nearly cancelled sums (dL/db is ~1e-4 of ||g|| here).
+    State gradient: the FP32 forward trajectory differs from the FP64 one by rounding, and
+    dL/du0 is sensitive to it: an FP64 co-state swept along the FP32 trajectory is already
+    ~2e-3 away from the FP64 reference, while the FP32 co-state arithmetic itself adds ~1e-7
+    (measured on the CPU).  The bound below is therefore 1e-2 normwise."""
+    N = 512
+    params = inp.default_params()
+    x = f32(inp.uniform_field(0, N, N))
+    target = inp.checkerboard(0, N, N)
+    uT, _ = gpu_run(rd, x, x, params, T, F32, "auto")
+    gu = f32(_mse_seed(uT, target))
+    du, dv, g = _gpu_adjoint(rd, x, x, params, T, gu, 0 * gu, F32)
+    ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, 0 * gu, nthreads=cpu_threads())
+    assert np.linalg.norm(g - og) <= 1e-4 * np.linalg.norm(og), dict(zip(NAMES, np.abs(g - og)))
+    assert normwise(du, ou) <= 1e-2 and normwise(dv, ov) <= 1e-2
+
+
+def test_f32_adjoint_short_horizon_is_tight(rd, oracle_mod):
+    """Over a short horizon the FP32 and FP64 trajectories agree to ~1e-7, so the FP32
+    adjoint must match the FP64 oracle closely: this isolates the adjoint arithmetic."""
+    N, T = 256, 20
+    params = inp.default_params()
+    x = f32(inp.uniform_field(3, N, N))
+    gu = f32(inp.uniform_field(4, N, N)) / (N * N)
+    gv = f32(inp.uniform_field(5, N, N)) / (N * N)
+    du, dv, g = _gpu_adjoint(rd, x, x, params, T, gu, gv, F32)
+    ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, gv)
+    assert normwise(du, ou) <= 1e-5 and normwise(dv, ov) <= 1e-5
+    np.testing.assert_allclose(g, og, rtol=1e-5, atol=1e-6 * np.linalg.norm(og))
+
+
+def test_f64_adjoint_full_size_512_T2000(rd, oracle_mod):
+    """The adjoint workload at full size (512^2, T = 2000, sqrt(T) = 45 checkpoints) in the
+    FP64 instantiation of the same kernels: rounding-order agreement with the oracle."""
+    N, T = 512, 2000
+    params = inp.default_params()
+    x = inp.uniform_field(0, N, N)
+    target = inp.checkerboard(0, N, N)
+    uT, _ = oracle_mod.run(x, x, params, T, nthreads=cpu_threads())
+    gu = _mse_seed(uT, target)
+    du, dv, g = _gpu_adjoint(rd, x, x, params, T, gu, 0 * gu, F64)
+    ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, 0 * gu, nthreads=cpu_threads())
+    assert normwise(du, ou) <= 1e-8 and normwise(dv, ov) <= 1e-8
+    np.testing.assert_allclose(g, og, rtol=1e-8, atol=1e-10 * np.linalg.norm(og))
+
+
+def test_autograd_function_gradcheck_f64(rd):
+    from torch.autograd import gradcheck
+
+    nn, nm, T = 6, 8, 5
+    u0 = _dev(inp.uniform_field(12, nn, nm), F64).requires_grad_()
+    v0 = _dev(inp.uniform_field(13, nn, nm), F64).requires_grad_()
+    p = inp.default_params()
+    theta = torch.tensor([p[k] for k in NAMES], dtype=F64, device="cuda", requires_grad=True)
+    f = lambda a, b, t: rd.RDCNNFunction.apply(a, b, t, T, p["dt"])  # noqa: E731
+    assert gradcheck(f, (u0, v0, theta), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_autograd_end_to_end_fit_step(rd):
+    """One gradient step on Du, Dv through RDCNNFunction lowers an MSE loss."""
+    N, T = 64, 60
+    p = inp.default_params()
+    x = _dev(f32(inp.uniform_field(0, N, N)), F32)
+    target = _dev(inp.checkerboard(0, N, N), F32)
+    theta = torch.tensor([p[k] for k in NAMES], dtype=F64, device="cuda", requires_grad=True)
+    uT, _ = rd.RDCNNFunction.apply(x, x, theta, T, p["dt"])
+    loss = torch.mean((uT - target) ** 2)
+    loss.backward()
+    assert torch.isfinite(theta.grad).all()
+    with torch.no_grad():
+        th2 = theta - 1e-3 * theta.grad / theta.grad.norm()
+    u2, _ = rd.RDCNNFunction.apply(x, x, th2, T, p["dt"])
+    assert torch.mean((u2 - target) ** 2).item() < loss.item()

@@ -1,0 +1,85 @@
+"""Batched sweep (one launch per k steps for all instances) vs the oracle and
+vs single-grid runs of the same instances (bit-identical: same cell arithmetic)."""
+import numpy as np
+import pytest
+import torch
+
+import rdcnn_inputs as inp
+from _util import cpu_threads, f32, gpu_run, normwise
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = torch.float32, torch.float64
+
+
+def _two_per_size(seed=0):
+    picked, seen = [], {}
+    for spec in inp.sweep_instances(seed):
+        if seen.get(spec["nn"], 0) < 2:
+            seen[spec["nn"]] = seen.get(spec["nn"], 0) + 1
+            picked.append(spec)
+    return sorted(picked, key=lambda s: s["nn"])
+
+
+def _load(batch, specs, dtype):
+    xs = []
+    for i, s in enumerate(specs):
+        x = inp.uniform_field(s["x_seed"], s["nn"], s["nm"])
+        if dtype == F32:
+            x = f32(x)
+        batch.set_state(i, torch.from_numpy(x), torch.from_numpy(x))
+        xs.append(x)
+    return xs
+
+
+def test_sweep_eight_instances_vs_oracle(rd, oracle_mod):
+    """Two instances of each size {128, 256, 512, 1024} from the seeded sweep, T = 500."""
+    specs = _two_per_size()
+    assert sorted(s["nn"] for s in specs) == [128, 128, 256, 256, 512, 512, 1024, 1024]
+    b = rd.Batch(specs, dtype=F32)
+    xs = _load(b, specs, F32)
+    b.run(500)
+    torch.cuda.synchronize()
+    for i, s in enumerate(specs):
+        ref_u, ref_v = oracle_mod.run(xs[i], xs[i], s["params"], 500, nthreads=cpu_threads())
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        assert normwise(u, ref_u) <= 1e-5 and normwise(v, ref_v) <= 1e-5, (i, s["nn"])
+
+
+@pytest.mark.parametrize("T,k", [(37, 4), (1, 4), (9, 1), (16, 8), (5, 6), (100, 3)])
+def test_batch_bitwise_equals_single_grid_runs(rd, T, k):
+    specs = [{"nn": 37, "nm": 64, "params": inp.default_params(Du=0.2, Dv=0.1)},
+             {"nn": 5, "nm": 8, "params": inp.default_params(a=0.1)},
+             {"nn": 128, "nm": 132, "params": inp.default_params(c=0.8, eps=-0.12)},
+             {"nn": 200, "nm": 256, "params": inp.default_params()}]
+    for i, s in enumerate(specs):
+        s["x_seed"] = 50 + i
+    b = rd.Batch(specs, dtype=F32)
+    b.set_tune(k=k)
+    xs = _load(b, specs, F32)
+    b.run(T)
+    torch.cuda.synchronize()
+    for i, s in enumerate(specs):
+        ref = gpu_run(rd, xs[i], xs[i], s["params"], T, F32, "generic")
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        assert np.array_equal(u, ref[0]) and np.array_equal(v, ref[1]), (i, T, k)
+
+
+def test_batch_f64_vs_oracle(rd, oracle_mod):
+    specs = [{"nn": n, "nm": m, "params": inp.default_params(Du=du), "x_seed": 70 + n}
+             for n, m, du in ((16, 16, 0.05), (40, 24, 0.2), (9, 130, 0.11))]
+    b = rd.Batch(specs, dtype=F64)
+    b.set_tune(k=3, rows=8)
+    xs = _load(b, specs, F64)
+    b.run(41)
+    torch.cuda.synchronize()
+    for i, s in enumerate(specs):
+        ref_u, ref_v = oracle_mod.run(xs[i], xs[i], s["params"], 41)
+        u, v = (t.cpu().numpy() for t in b.state(i))
+        assert normwise(u, ref_u) <= 1e-12 and normwise(v, ref_v) <= 1e-12
+
+
+def test_batch_rejects_bad_instance(rd):
+    with pytest.raises(rd.RDCNNError):
+        b = rd.Batch([{"nn": 8, "nm": 6}], dtype=F32)
+        b.run(3)
