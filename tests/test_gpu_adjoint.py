@@ -84,13 +84,16 @@ def _mse_seed(uT, target):
     return 2.0 * (uT - target) / uT.size
 
 
-@pytest.mark.parametrize("T", [200, 2000])
-def test_f32_checkerboard_mse_512(rd, oracle_mod, T):
+@pytest.mark.parametrize("T,gtol", [(200, 1e-3), (2000, 1e-4)])
+def test_f32_checkerboard_mse_512(rd, oracle_mod, T, gtol):
     """512^2 FP32, MSE(u_T, checkerboard of period 32), sqrt(T) checkpoints.
 
-    Gene gradient: ||g_gpu - g_ref|| / ||g_ref|| <= 1e-4 against the FP64 oracle adjoint
-    (which is pinned to FP64 finite differences).  The vector norm is the measure: single
-    entries can be nearly cancelled sums (dL/db is ~1e-4 of ||g|| here).
+    Gene gradient: ||g_gpu - g_ref|| / ||g_ref|| <= 1e-4 at the workload's horizon T = 2000
+    against the FP64 oracle adjoint (which is pinned to FP64 finite differences).  The
+    vector norm is the measure: single entries can be nearly cancelled sums (dL/db is
+    ~1e-4 of ||g|| at T = 200).  At T = 200 the field is mid-transient and the FP32
+    trajectory itself is ill-conditioned (FP64 co-state along an FP32 trajectory:
+    7e-5 on the CPU, 2.4e-4 with the GPU's rounding order), so that horizon gets 1e-3.
     State gradient: the FP32 forward trajectory differs from the FP64 one by rounding, and
     dL/du0 is sensitive to it: an FP64 co-state swept along the FP32 trajectory is already
     ~2e-3 away from the FP64 reference, while the FP32 co-state arithmetic itself adds ~1e-7
@@ -103,7 +106,7 @@ def test_f32_checkerboard_mse_512(rd, oracle_mod, T):
     gu = f32(_mse_seed(uT, target))
     du, dv, g = _gpu_adjoint(rd, x, x, params, T, gu, 0 * gu, F32)
     ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, 0 * gu, nthreads=cpu_threads())
-    assert np.linalg.norm(g - og) <= 1e-4 * np.linalg.norm(og), dict(zip(NAMES, np.abs(g - og)))
+    assert np.linalg.norm(g - og) <= gtol * np.linalg.norm(og), dict(zip(NAMES, np.abs(g - og)))
     assert normwise(du, ou) <= 1e-2 and normwise(dv, ov) <= 1e-2
 
 
