@@ -29,15 +29,24 @@ namespace {
 
 constexpr int kAdjBlock = 256;
 
+// Coefficients of the reverse step, arranged like the forward cell update
+// (the -4 centre weight folded in): cm4 = c - 4 Du, ebm4 = eps b - 4 Dv;
+// with no reaction cm4 = -4 Du, ebm4 = -4 Dv and the rest is unused.
+// a, b, eps (FP64) enter only the gradient sums.
 template <typename T> struct AdjCoef {
-    T dt, a, b, eps, c, Du, Dv, meps, epsb;
+    T dt, Du, Dv, cm4, meps, ebm4;
+    double a, b, eps;
 };
 
 template <typename T>
-AdjCoef<T> make_adj_coef(const rdcnn_params &p) {
+AdjCoef<T> make_adj_coef(const rdcnn_params &p, int reaction) {
+    const bool fhn = (reaction == RDCNN_REACTION_FHN);
     AdjCoef<T> q;
-    q.dt = T(p.dt); q.a = T(p.a); q.b = T(p.b); q.eps = T(p.eps); q.c = T(p.c);
-    q.Du = T(p.Du); q.Dv = T(p.Dv); q.meps = T(-p.eps); q.epsb = T(p.eps * p.b);
+    q.dt = T(p.dt); q.Du = T(p.Du); q.Dv = T(p.Dv);
+    q.cm4 = T((fhn ? p.c : 0.0) - 4.0 * p.Du);
+    q.meps = T(fhn ? -p.eps : 0.0);
+    q.ebm4 = T((fhn ? p.eps * p.b : 0.0) - 4.0 * p.Dv);
+    q.a = p.a; q.b = p.b; q.eps = p.eps;
     return q;
 }
 
@@ -50,11 +59,6 @@ template <typename T>
 __device__ __forceinline__ void load4(Slice4<T> &s, const T *const (&src)[4], int64_t off) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) load_vec<T>(s.f[q], src[q] + off);
-}
-
-template <typename T>
-__device__ __forceinline__ T lap5(T c, T n, T s, T w, T e) {
-    return fma_rn(T(-4), c, add_rn(add_rn(n, s), add_rn(w, e)));
 }
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -116,31 +120,34 @@ k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__rest
         T ou[V], ov[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            T lap[4];
+            T nsum[4];  // neighbour sums (n + s) + (w + e)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const T w = (e == 0) ? west[q] : cen.f[q][e - 1];
                 const T ea = (e == V - 1) ? east[q] : cen.f[q][e + 1];
-                lap[q] = lap5(cen.f[q][e], nor.f[q][e], sou.f[q][e], w, ea);
+                nsum[q] = add_rn(add_rn(nor.f[q][e], sou.f[q][e]), add_rn(w, ea));
             }
             const T uc = cen.f[0][e], vc = cen.f[1][e], luc = cen.f[2][e], lvc = cen.f[3][e];
+            // co-state update with the centre term folded in, like the forward:
+            //   lu + dt [ Du s(lu) + (c - 4 Du - u^2) lu - eps lv ]
+            //   lv + dt [ Dv s(lv) + (eps b - 4 Dv) lv - lu ]
             T ru, rv;
             if (RX == RX_FHN) {
-                ru = fma_rn(fma_rn(-uc, uc, p.c), luc, mul_rn(p.meps, lvc));   // (c - u^2) lu - eps lv
-                rv = fma_rn(p.epsb, lvc, -luc);                                 // -lu + eps b lv
+                ru = fma_rn(fma_rn(-uc, uc, p.cm4), luc, mul_rn(p.meps, lvc));
+                rv = fma_rn(p.ebm4, lvc, -luc);
             } else {
-                ru = T(0);
-                rv = T(0);
+                ru = mul_rn(p.cm4, luc);
+                rv = mul_rn(p.ebm4, lvc);
             }
-            ou[e] = fma_rn(p.dt, fma_rn(p.Du, lap[2], ru), luc);
-            ov[e] = fma_rn(p.dt, fma_rn(p.Dv, lap[3], rv), lvc);
+            ou[e] = fma_rn(p.dt, fma_rn(p.Du, nsum[2], ru), luc);
+            ov[e] = fma_rn(p.dt, fma_rn(p.Dv, nsum[3], rv), lvc);
             if (active) {
                 const double L = (double)luc, M = (double)lvc;
-                g[0] += L * (double)lap[0];
-                g[1] += M * (double)lap[1];
+                g[0] += L * ((double)nsum[0] - 4.0 * (double)uc);   // lu Lap(u)
+                g[1] += M * ((double)nsum[1] - 4.0 * (double)vc);   // lv Lap(v)
                 if (RX == RX_FHN) {
                     const double du = (double)uc, dv = (double)vc;
-                    const double eps = (double)p.eps, b = (double)p.b, a = (double)p.a;
+                    const double eps = p.eps, b = p.b, a = p.a;
                     g[2] += M * (-eps);
                     g[3] += M * (eps * dv);
                     g[4] += M * (-(du - b * dv + a));
@@ -204,7 +211,7 @@ cudaError_t adjoint_step_t(int reaction, const void *u, const void *v, const voi
                            int64_t nm, const rdcnn_params &p, const AdjShape &sh, cudaStream_t s) {
     const int wpb = kAdjBlock / 32;
     const unsigned grid = (unsigned)((sh.nwarps + wpb - 1) / wpb);
-    const AdjCoef<T> c = make_adj_coef<T>(p);
+    const AdjCoef<T> c = make_adj_coef<T>(p, reaction);
     if (reaction == RDCNN_REACTION_FHN)
         k_adjoint_step<T, RX_FHN><<<grid, kAdjBlock, 0, s>>>(
             (const T *)u, (const T *)v, (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, partial,

@@ -31,7 +31,7 @@ struct BatchDesc {
     void *su, *sv;
     int nn, nm, bands, rows;
     long long warp_begin;
-    double dt, a, b, eps, c, Du, Dv;
+    double dt, Du, Dv, cm4, mthird, meps, ebm4, mepsa;  // as Coef<double>
 };
 
 template <typename T, int K, int H, int RX>
@@ -48,8 +48,8 @@ k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int
     const int local = (int)(wid - d.warp_begin);
     const int bands = d.bands;
     Coef<T> p;
-    p.dt = T(d.dt); p.a = T(d.a); p.mb = T(-d.b); p.meps = T(-d.eps); p.c = T(d.c);
-    p.Du = T(d.Du); p.Dv = T(d.Dv); p.mthird = T(-1.0 / 3.0);
+    p.dt = T(d.dt); p.Du = T(d.Du); p.Dv = T(d.Dv); p.cm4 = T(d.cm4);
+    p.mthird = T(d.mthird); p.meps = T(d.meps); p.ebm4 = T(d.ebm4); p.mepsa = T(d.mepsa);
     const T *su = (const T *)(flip ? d.su : d.u);
     const T *sv = (const T *)(flip ? d.sv : d.v);
     T *du = (T *)(flip ? d.u : d.su);
@@ -202,8 +202,9 @@ int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int
         const long long strips = (x.nn + d.rows - 1) / d.rows;
         d.warp_begin = warps;
         warps += (long long)d.bands * strips;
-        d.dt = x.params.dt; d.a = x.params.a; d.b = x.params.b; d.eps = x.params.eps;
-        d.c = x.params.c; d.Du = x.params.Du; d.Dv = x.params.Dv;
+        const Coef<double> q = make_coef<double>(x.params, reaction);
+        d.dt = q.dt; d.Du = q.Du; d.Dv = q.Dv; d.cm4 = q.cm4;
+        d.mthird = q.mthird; d.meps = q.meps; d.ebm4 = q.ebm4; d.mepsa = q.mepsa;
     }
     cudaError_t e = cudaMemcpyAsync(workspace, tab.data(), n * sizeof(BatchDesc),
                                     cudaMemcpyHostToDevice, s);

@@ -164,7 +164,7 @@ cudaError_t step1_t(int reaction, const void *u, const void *v, void *un, void *
     const int64_t nwarps = (int64_t)bands * strips;
     const int wpb = kStep1Block / 32;
     const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    const Coef<T> c = make_coef<T>(p);
+    const Coef<T> c = make_coef<T>(p, reaction);
     if (reaction == RDCNN_REACTION_FHN)
         k_step1<T, RX_FHN><<<grid, kStep1Block, 0, s>>>((const T *)u, (const T *)v, (T *)un,
                                                         (T *)vn, (int)nn, (int)nm, bands,
@@ -188,7 +188,7 @@ cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, vo
     const int64_t nwarps = (int64_t)bands * strips;
     const int wpb = kTemporalBlock / 32;
     const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    const Coef<T> c = make_coef<T>(p);
+    const Coef<T> c = make_coef<T>(p, reaction);
     if (reaction == RDCNN_REACTION_FHN)
         k_temporal<T, K, RX_FHN><<<grid, kTemporalBlock, 0, s>>>(
             (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps,
@@ -207,7 +207,7 @@ cudaError_t generic_t(int reaction, const void *u, const void *v, void *un, void
     const int64_t n = nn * nm;
     const int64_t want = (n + 255) / 256;
     const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)sm_count() * 16);
-    const Coef<T> c = make_coef<T>(p);
+    const Coef<T> c = make_coef<T>(p, reaction);
     if (reaction == RDCNN_REACTION_FHN)
         k_generic<T, RX_FHN><<<grid, 256, 0, s>>>((const T *)u, (const T *)v, (T *)un, (T *)vn,
                                                   (int)nn, (int)nm, c);
