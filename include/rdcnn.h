@@ -186,6 +186,40 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
                   void *dLdu0, void *dLdv0, double grad[6],
                   void *workspace, size_t workspace_bytes);
 
+/* ------------------------------------------------------------------ no-allocation run */
+
+/* Bytes of the fixed device array rdcnn_run_static uses as scratch. */
+#define RDCNN_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* rdcnn_run for callers that cannot allocate device memory.  The paper has no
+ * counterpart: it exists for hosts that own the whole device memory pool
+ * (plug-ins inside another framework, which forbids or cannot budget extra
+ * cudaMalloc calls) and for C/Fortran drivers that only receive device
+ * pointers from another component, and so cannot supply the scratch
+ * workspace rdcnn_bind asks for.
+ *
+ * Advances the caller's state planes u, v (device, NN x NM, dtype, updated in
+ * place) by T steps of the same update as rdcnn_run (temporal kernel when NM
+ * is a multiple of 4 / 2 and u, v are 16-byte aligned, generic otherwise;
+ * k = steps per launch, 0 = default), asynchronously on `stream`.  The two
+ * ping-pong planes live in one file-scope __device__ array of
+ * RDCNN_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading this library
+ * holds until the process exits, so NN * NM * sizeof(element) may be at most
+ * 8 MiB (2,097,152 FP32 or 1,048,576 FP64 cells); larger grids return
+ * RDCNN_EINVAL before any GPU work.  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).
+ * All calls share that one array and it keeps the last call's contents
+ * (nothing in it needs to start at zero): calls whose GPU work overlaps in
+ * time -- other streams or other host threads on the same device -- race on
+ * it and must be serialised by the caller.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress, which may load
+ * the library's module on that device); make that first call before any
+ * stream capture begins on the device.
+ * Errors: RDCNN_EINVAL, RDCNN_ENONFINITE, RDCNN_ECUDA; RDCNN_WARN_CFL as for
+ * rdcnn_create. */
+int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, int reaction,
+                     void *u, void *v, int64_t T, int k, void *stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 
 /* Description of the last error on the calling thread ("" if none). */

@@ -37,6 +37,7 @@ VARIANT_TEMPORAL = 2
 VARIANT_GENERIC = 3
 
 PARAM_FIELDS = ("dt", "a", "b", "eps", "c", "Du", "Dv")
+STATIC_SCRATCH_BYTES = 16 << 20  # RDCNN_STATIC_SCRATCH_BYTES
 
 
 class Params(ctypes.Structure):
@@ -71,6 +72,8 @@ SIGNATURES = [
     ("rdcnn_adjoint_workspace_bytes", c_int, [c_vp, c_i64, c_i64, ctypes.POINTER(c_size)]),
     ("rdcnn_adjoint", c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,
                               ctypes.POINTER(c_double), c_vp, c_size]),
+    ("rdcnn_run_static", c_int, [c_i64, c_i64, ctypes.POINTER(Params), c_int, c_int, c_vp, c_vp, c_i64,
+                                 c_int, c_vp]),
     ("rdcnn_last_error", ctypes.c_char_p, []),
     ("rdcnn_launch_count", ctypes.c_uint64, []),
     ("rdcnn_version", ctypes.c_char_p, []),

@@ -229,6 +229,27 @@ def run(u: torch.Tensor, v: torch.Tensor, params: dict | None, T: int, variant: 
     return u, v
 
 
+def run_static(u: torch.Tensor, v: torch.Tensor, params: dict | None, T: int, k: int = 0,
+               reaction: str = "fhn"):
+    """Advance (u, v) in place by T steps without any scratch allocation.
+
+    For callers that cannot allocate device memory: the ping-pong planes come
+    from the library's fixed 16 MiB device array (grids up to 8 MiB per plane).
+    Calls that overlap on the GPU share that array and race; serialise them.
+    """
+    if u.shape != v.shape or u.dim() != 2:
+        raise ValueError("u and v must be 2-D planes of the same shape")
+    nn, nm = u.shape
+    _plane_check(u, nn, nm, u.dtype, "u")
+    _plane_check(v, nn, nm, u.dtype, "v")
+    ps = L.params_struct(_params(params))
+    rc = L.check(L.load().rdcnn_run_static(nn, nm, ctypes.byref(ps), _dtype_code(u.dtype),
+                                           _REACTIONS[reaction], _vp(u), _vp(v), int(T), int(k),
+                                           ctypes.c_void_p(_stream_ptr(u.device))))
+    _warn(rc)
+    return u, v
+
+
 class Batch:
     """A set of independent instances advanced together by ``rdcnn_batch_run``.
 
