@@ -24,7 +24,7 @@ namespace rdk {
 
 namespace {
 
-constexpr int kBatchBlock = 128;
+constexpr int kBatchBlock = 32 * kTemporalWarps;
 
 struct BatchDesc {
     const void *u, *v;

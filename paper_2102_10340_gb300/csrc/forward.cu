@@ -31,7 +31,7 @@ namespace rdk {
 namespace {
 
 constexpr int kStep1Block = 256;
-constexpr int kTemporalBlock = 128;
+constexpr int kTemporalBlock = 32 * kTemporalWarps;
 
 // --------------------------------------------------------------------------- single step
 

@@ -5,8 +5,10 @@
 // [band*OUTW, band*OUTW + OUTW) and output rows [strip*rows, strip*rows + rows)
 // of an NN x NM torus.  It loads 32*V columns starting H*V columns to the left
 // of its band (H = ceil(K/V) halo lanes per side, indices wrapped modulo NM)
-// and input rows r0-K .. r0+rows+K-1 (wrapped modulo NN).  Each input row
-// passes through K stages held in registers; stage s turns rows (q-1, q, q+1)
+// and input rows r0-K .. r0+rows+K-1 (wrapped modulo NN).  Input rows are
+// staged through a per-warp shared-memory ring by cp.async, kRing - 1 rows
+// ahead of use.  Each input row passes through K stages held in registers;
+// stage s turns rows (q-1, q, q+1)
 // of stage s-1 into row q of stage s.  After K stages the K outermost columns
 // on each side are stale, which is why only lanes H .. 31-H store.
 #pragma once
@@ -15,23 +17,73 @@
 
 namespace rdk {
 
-// One pipeline beat: consume input row m of the strip, advance every stage by
-// one row, and store the finished row (stage K) when it is inside the strip.
-// W[PH], W[PH+1] hold the two older rows of each stage, W[PH+2] receives the
-// newest, so a 3-beat unroll rotates the windows without register moves.
+constexpr int kTemporalWarps = 4;  // warps per block of every kernel built on temporal_strip
+constexpr int kRing = 4;           // input rows staged per warp (prefetch distance kRing - 1)
+
+// Per-lane 16-byte asynchronous global -> shared copy (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory ring of one warp: kRing rows x {u, v} x 32 lanes x 16 bytes.
+// Each lane copies and later reads back only its own 16 bytes, so the lane's
+// own cp.async.wait_group is the only synchronisation needed.
+template <typename T> struct RowRing {
+    typedef typename Vec<T>::type VT;
+    VT (*slot)[2][32];  // [kRing][field][lane]
+};
+
+template <typename T>
+__device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, int nm, int lc,
+                                           const T *__restrict__ u, const T *__restrict__ v) {
+    const int lane = threadIdx.x & 31;
+    const int64_t off = (int64_t)g * nm + lc;
+    cp_async16(&r.slot[m % kRing][0][lane], u + off);
+    cp_async16(&r.slot[m % kRing][1][lane], v + off);
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<T> &s) {
+    typedef typename Vec<T>::type VT;
+    const int lane = threadIdx.x & 31;
+    const VT a = r.slot[m % kRing][0][lane];
+    const VT b = r.slot[m % kRing][1][lane];
+    if constexpr (Vec<T>::N == 4) {
+        s.u[0] = a.x; s.u[1] = a.y; s.u[2] = a.z; s.u[3] = a.w;
+        s.v[0] = b.x; s.v[1] = b.y; s.v[2] = b.z; s.v[3] = b.w;
+    } else {
+        s.u[0] = a.x; s.u[1] = a.y;
+        s.v[0] = b.x; s.v[1] = b.y;
+    }
+}
+
+// One pipeline beat: take input row m of the strip from the ring (issuing the
+// copy of row m + kRing - 1 first), advance every stage by one row, and store
+// the finished row (stage K) when it is inside the strip.  W[PH], W[PH+1] hold
+// the two older rows of each stage, W[PH+2] receives the newest, so a 3-beat
+// unroll rotates the windows without register moves.
 template <typename T, int K, int RX, int PH>
 __device__ __forceinline__ void temporal_beat(int m, int total, Slice<T> (&W)[3][K],
-                                              Slice<T> &nxt, int &g, int nn, int nm, int lc,
-                                              const T *__restrict__ u, const T *__restrict__ v,
+                                              const RowRing<T> &ring, int &g_issue, int nn, int nm,
+                                              int lc, const T *__restrict__ u, const T *__restrict__ v,
                                               T *__restrict__ un, T *__restrict__ vn,
                                               int r0, int sc, bool st_lane, const Coef<T> &p) {
     constexpr int V = Vec<T>::N;
     if (m >= total) return;
-    Slice<T> cur = nxt;
-    if (m + 1 < total) {
-        g = (g + 1 == nn) ? 0 : g + 1;
-        load_slice(nxt, u, v, (int64_t)g * nm + lc);
+    // The slot written here was read in the previous beat, whose stage
+    // computations (issued before this point) consumed that value.
+    if (m + kRing - 1 < total) {
+        ring_issue(ring, m + kRing - 1, g_issue, nm, lc, u, v);
+        g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
     }
+    cp_async_commit();
+    cp_async_wait<kRing - 1>();  // the group holding row m is complete
+    Slice<T> cur;
+    ring_read(ring, m, cur);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
         Slice<T> &A = W[PH][s];
@@ -80,14 +132,27 @@ __device__ __forceinline__ void temporal_strip(int band, int strip, const T *__r
 #pragma unroll
         for (int s = 0; s < K; ++s) zero_slice(W[a][s]);
 
-    int g = wrap_row((int64_t)r0 - K, nn);
-    Slice<T> nxt;
-    load_slice(nxt, u, v, (int64_t)g * nm + lc);
-    for (int m = 0; m < total; m += 3) {
-        temporal_beat<T, K, RX, 0>(m, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
-        temporal_beat<T, K, RX, 1>(m + 1, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
-        temporal_beat<T, K, RX, 2>(m + 2, total, W, nxt, g, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+    typedef typename Vec<T>::type VT;
+    __shared__ __align__(16) VT ring_mem[kTemporalWarps][kRing][2][32];
+    RowRing<T> ring;
+    ring.slot = ring_mem[(threadIdx.x >> 5) % kTemporalWarps];
+
+    // prologue: rows 0 .. kRing-2 in flight, one commit group each
+    int g_issue = wrap_row((int64_t)r0 - K, nn);
+#pragma unroll
+    for (int j = 0; j < kRing - 1; ++j) {
+        if (j < total) {
+            ring_issue(ring, j, g_issue, nm, lc, u, v);
+            g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+        }
+        cp_async_commit();
     }
+    for (int m = 0; m < total; m += 3) {
+        temporal_beat<T, K, RX, 0>(m, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+        temporal_beat<T, K, RX, 1>(m + 1, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+        temporal_beat<T, K, RX, 2>(m + 2, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+    }
+    cp_async_wait<0>();
 }
 
 }  // namespace rdk
