@@ -50,23 +50,19 @@ AdjCoef<T> make_adj_coef(const rdcnn_params &p, int reaction) {
     return q;
 }
 
-// A lane's slice of one row for the four fields the reverse step reads.
-template <typename T> struct Slice4 {
-    T f[4][Vec<T>::N];  // 0 = u, 1 = v, 2 = lu, 3 = lv
-};
-
-template <typename T>
-__device__ __forceinline__ void load4(Slice4<T> &s, const T *const (&src)[4], int64_t off) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) load_vec<T>(s.f[q], src[q] + off);
-}
-
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     return x;
 }
 
+// One reverse step for a (band, strip) of rows.  The co-state (lu, lv) is
+// streamed with a 3-row window plus one prefetched row (Slice<T>.u = lu,
+// .v = lv); the state (u, v) at the same time level is needed only at the
+// centre cell.  The Du / Dv gradient terms use the symmetry of the periodic
+// Laplacian, sum_k lu_k Lap(u)_k = sum_k u_k Lap(lu)_k, so they reuse the
+// co-state neighbour sums the update forms anyway.  Per-row sums of the six
+// gene terms are formed in T and accumulated in FP64.
 template <typename T, int RX>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ lu,
@@ -87,47 +83,55 @@ k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__rest
     const bool edge_e = active && (lane == 31 || col + V >= nm);
     const int r0 = strip * rows;
     const int r1 = min(r0 + rows, nn);
-    const T *const src[4] = {u, v, lu, lv};
 
-    Slice4<T> nor, cen, sou;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int e = 0; e < V; ++e) nor.f[q][e] = cen.f[q][e] = sou.f[q][e] = T(0);
-    int rn = (r0 == 0) ? nn - 1 : r0 - 1;
+    Slice<T> nor, cen, sou, pre, st, st_pre;  // co-state rows r-1, r, r+1, r+2; state rows r, r+1
+    zero_slice(nor); zero_slice(cen); zero_slice(sou); zero_slice(pre); zero_slice(st); zero_slice(st_pre);
+    T cw_u = 0, ce_u = 0, cw_v = 0, ce_v = 0, sw_u = 0, se_u = 0, sw_v = 0, se_v = 0;
+    T pw_u = 0, pe_u = 0, pw_v = 0, pe_v = 0;
+    const int rn = (r0 == 0) ? nn - 1 : r0 - 1;
     int rs = (r0 + 1 == nn) ? 0 : r0 + 1;
     if (active) {
-        load4(nor, src, (int64_t)rn * nm + col);
-        load4(cen, src, (int64_t)r0 * nm + col);
+        load_slice(nor, lu, lv, (int64_t)rn * nm + col);
+        load_slice(cen, lu, lv, (int64_t)r0 * nm + col);
+        load_slice(sou, lu, lv, (int64_t)rs * nm + col);
+        load_slice(st, u, v, (int64_t)r0 * nm + col);
+    }
+    if (edge_w) {
+        cw_u = __ldg(lu + (int64_t)r0 * nm + colw); cw_v = __ldg(lv + (int64_t)r0 * nm + colw);
+        sw_u = __ldg(lu + (int64_t)rs * nm + colw); sw_v = __ldg(lv + (int64_t)rs * nm + colw);
+    }
+    if (edge_e) {
+        ce_u = __ldg(lu + (int64_t)r0 * nm + cole); ce_v = __ldg(lv + (int64_t)r0 * nm + cole);
+        se_u = __ldg(lu + (int64_t)rs * nm + cole); se_v = __ldg(lv + (int64_t)rs * nm + cole);
     }
     double g[6] = {0, 0, 0, 0, 0, 0};
     for (int r = r0; r < r1; ++r) {
-        if (active) load4(sou, src, (int64_t)rs * nm + col);
-        T west[4], east[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            west[q] = __shfl_up_sync(kFull, cen.f[q][V - 1], 1);
-            east[q] = __shfl_down_sync(kFull, cen.f[q][0], 1);
+        const bool more = (r + 1 < r1);
+        const int rp = (rs + 1 == nn) ? 0 : rs + 1;
+        if (more) {
+            if (active) {
+                load_slice(pre, lu, lv, (int64_t)rp * nm + col);
+                load_slice(st_pre, u, v, (int64_t)rs * nm + col);
+            }
+            if (edge_w) { pw_u = __ldg(lu + (int64_t)rp * nm + colw); pw_v = __ldg(lv + (int64_t)rp * nm + colw); }
+            if (edge_e) { pe_u = __ldg(lu + (int64_t)rp * nm + cole); pe_v = __ldg(lv + (int64_t)rp * nm + cole); }
         }
-        if (edge_w) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) west[q] = __ldg(src[q] + (int64_t)r * nm + colw);
-        }
-        if (edge_e) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) east[q] = __ldg(src[q] + (int64_t)r * nm + cole);
-        }
+        T wu = __shfl_up_sync(kFull, cen.u[V - 1], 1);
+        T eu = __shfl_down_sync(kFull, cen.u[0], 1);
+        T wv = __shfl_up_sync(kFull, cen.v[V - 1], 1);
+        T ev = __shfl_down_sync(kFull, cen.v[0], 1);
+        if (edge_w) { wu = cw_u; wv = cw_v; }
+        if (edge_e) { eu = ce_u; ev = ce_v; }
         T ou[V], ov[V];
+        T rg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            T nsum[4];  // neighbour sums (n + s) + (w + e)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T w = (e == 0) ? west[q] : cen.f[q][e - 1];
-                const T ea = (e == V - 1) ? east[q] : cen.f[q][e + 1];
-                nsum[q] = add_rn(add_rn(nor.f[q][e], sou.f[q][e]), add_rn(w, ea));
-            }
-            const T uc = cen.f[0][e], vc = cen.f[1][e], luc = cen.f[2][e], lvc = cen.f[3][e];
+            const T luc = cen.u[e], lvc = cen.v[e];
+            const T su = add_rn(add_rn(nor.u[e], sou.u[e]), add_rn(e == 0 ? wu : cen.u[e - 1],
+                                                                   e == V - 1 ? eu : cen.u[e + 1]));
+            const T sv = add_rn(add_rn(nor.v[e], sou.v[e]), add_rn(e == 0 ? wv : cen.v[e - 1],
+                                                                   e == V - 1 ? ev : cen.v[e + 1]));
+            const T uc = st.u[e], vc = st.v[e];
             // co-state update with the centre term folded in, like the forward:
             //   lu + dt [ Du s(lu) + (c - 4 Du - u^2) lu - eps lv ]
             //   lv + dt [ Dv s(lv) + (eps b - 4 Dv) lv - lu ]
@@ -139,30 +143,34 @@ k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__rest
                 ru = mul_rn(p.cm4, luc);
                 rv = mul_rn(p.ebm4, lvc);
             }
-            ou[e] = fma_rn(p.dt, fma_rn(p.Du, nsum[2], ru), luc);
-            ov[e] = fma_rn(p.dt, fma_rn(p.Dv, nsum[3], rv), lvc);
-            if (active) {
-                const double L = (double)luc, M = (double)lvc;
-                g[0] += L * ((double)nsum[0] - 4.0 * (double)uc);   // lu Lap(u)
-                g[1] += M * ((double)nsum[1] - 4.0 * (double)vc);   // lv Lap(v)
-                if (RX == RX_FHN) {
-                    const double du = (double)uc, dv = (double)vc;
-                    const double eps = p.eps, b = p.b, a = p.a;
-                    g[2] += M * (-eps);
-                    g[3] += M * (eps * dv);
-                    g[4] += M * (-(du - b * dv + a));
-                    g[5] += L * du;
-                }
+            ou[e] = fma_rn(p.dt, fma_rn(p.Du, su, ru), luc);
+            ov[e] = fma_rn(p.dt, fma_rn(p.Dv, sv, rv), lvc);
+            rg[0] = fma_rn(uc, fma_rn(T(-4), luc, su), rg[0]);     // u Lap(lu)
+            rg[1] = fma_rn(vc, fma_rn(T(-4), lvc, sv), rg[1]);     // v Lap(lv)
+            if (RX == RX_FHN) {
+                rg[2] = add_rn(rg[2], lvc);                        // lv        (x -eps)
+                rg[3] = fma_rn(lvc, vc, rg[3]);                    // lv v      (x eps)
+                rg[4] = fma_rn(lvc, fma_rn(T(-p.b), vc, uc), rg[4]);  // lv (u - b v)
+                rg[5] = fma_rn(luc, uc, rg[5]);                    // lu u
             }
         }
         if (active) {
             const int64_t off = (int64_t)r * nm + col;
             store_vec<T>(lun + off, ou);
             store_vec<T>(lvn + off, ov);
+            g[0] += (double)rg[0];
+            g[1] += (double)rg[1];
+            if (RX == RX_FHN) {
+                g[2] -= p.eps * (double)rg[2];
+                g[3] += p.eps * (double)rg[3];
+                g[4] -= (double)rg[4] + p.a * (double)rg[2];
+                g[5] += (double)rg[5];
+            }
         }
-        nor = cen;
-        cen = sou;
-        rs = (rs + 1 == nn) ? 0 : rs + 1;
+        nor = cen; cen = sou; sou = pre; st = st_pre;
+        cw_u = sw_u; ce_u = se_u; cw_v = sw_v; ce_v = se_v;
+        sw_u = pw_u; se_u = pe_u; sw_v = pw_v; se_v = pe_v;
+        rs = rp;
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
@@ -189,7 +197,11 @@ k_reduce_partials(const double *__restrict__ partial, int nwarps, double dt, dou
     }
 }
 
-int adj_rows(int64_t nn) { return nn >= 1024 ? 32 : 16; }
+// Rows per warp: enough warps to fill the GPU (~2048), at most 16 rows.
+int adj_rows(int64_t nn, int bands) {
+    const int64_t r = nn * bands / 2048;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, r));
+}
 
 struct AdjShape {
     int bands, strips, nwarps, rows;
@@ -198,8 +210,8 @@ struct AdjShape {
 AdjShape adj_shape(int dtype, int64_t nn, int64_t nm) {
     AdjShape s;
     const int V = vec_width(dtype);
-    s.rows = adj_rows(nn);
     s.bands = (int)((nm + 32 * V - 1) / (32 * V));
+    s.rows = adj_rows(nn, s.bands);
     s.strips = (int)((nn + s.rows - 1) / s.rows);
     s.nwarps = s.bands * s.strips;
     return s;
@@ -294,8 +306,8 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     double *partial = (double *)(ws + L.part_off);
     double *gout = (double *)(ws + L.out_off);
     const AdjShape sh = adj_shape(dtype, nn, nm);
-    const int k = default_k(dtype);
-    const int rows_t = default_rows_temporal(dtype, k, nn, nm);
+    const int k = default_k(dtype, nn, nm);
+    const int rows_t = 0;  // chosen by the launcher
     const int rows_1 = default_rows_step1(dtype, nn, nm);
 
     cudaError_t e = cudaMemcpyAsync(lam_u[0], dLdu_T, bytes, cudaMemcpyDeviceToDevice, s);

@@ -191,7 +191,7 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
                          "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
                          vec_width(h->dtype));
     if (variant == RDCNN_VARIANT_TEMPORAL) {
-        if (k == 0) k = h->tune_k ? h->tune_k : default_k(h->dtype);
+        if (k == 0) k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
         if (k < 1 || k > max_k(h->dtype))
             return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(h->dtype));
     } else {
@@ -205,8 +205,7 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
         cudaError_t e;
         if (variant == RDCNN_VARIANT_TEMPORAL)
             e = launch_temporal(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
-                                h->tune_rows ? h->tune_rows : default_rows_temporal(h->dtype, kk, h->nn, h->nm),
-                                h->stream);
+                                h->tune_rows, h->stream);  // 0 = chosen by the launcher
         else if (variant == RDCNN_VARIANT_STEP1)
             e = launch_step1(h->dtype, h->reaction, cu, cv, nu, nv, h->nn, h->nm, h->p,
                              h->tune_rows ? h->tune_rows : default_rows_step1(h->dtype, h->nn, h->nm),

@@ -146,7 +146,7 @@ int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, i
 }
 
 int resolve_tune(const rdcnn_tune *tune, int dtype, int *k, int *rows) {
-    *k = (tune && tune->k) ? tune->k : default_k(dtype);
+    *k = (tune && tune->k) ? tune->k : std::min(4, max_k(dtype));
     *rows = (tune && tune->rows) ? tune->rows : 0;
     if (*k < 1 || *k > max_k(dtype)) return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(dtype));
     if (*rows < 0) return set_error(RDCNN_EINVAL, "rows must be >= 0");

@@ -177,6 +177,44 @@ cudaError_t step1_t(int reaction, const void *u, const void *v, void *un, void *
     return cudaGetLastError();
 }
 
+// Rows per warp strip when the caller gives none.  Small grids use short
+// strips (few warps exist at all); large grids pick, among a few lengths,
+// the one that minimises waves x (rows + 2K) -- the work of the slowest SM
+// when every resident warp slot is busy -- so a launch does not spill a
+// nearly empty second wave (e.g. 4096^2, K=8: 128 rows = 1184 warps, one
+// wave on 152 SMs at 8 warps each; 112 rows = 1369 warps, two waves).
+int auto_rows_temporal(int K, int64_t nn, int64_t nm, int bands, int blocks_per_sm,
+                       int warps_per_block) {
+    const int64_t cells = nn * nm;
+    if (cells < (int64_t(1) << 17)) return 4;
+    if (cells < (int64_t(1) << 19)) return 8;
+    if (cells < (int64_t(1) << 22)) return 16;
+    const int64_t cap = (int64_t)sm_count() * std::max(1, blocks_per_sm) * warps_per_block;
+    static const int cand[] = {32, 48, 64, 96, 128, 160, 192, 256};
+    int best = 64;
+    double best_cost = 1e300;
+    for (int r : cand) {
+        const int64_t warps = (int64_t)bands * ((nn + r - 1) / r);
+        const int64_t waves = (warps + cap - 1) / cap;
+        const double cost = (double)waves * (double)(std::min<int64_t>(r, nn) + 2 * K);
+        if (cost < best_cost) { best_cost = cost; best = r; }
+    }
+    return best;
+}
+
+template <typename T, int K, int RX>
+int temporal_blocks_per_sm() {
+    static int cached = -1;
+    if (cached < 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_temporal<T, K, RX>, kTemporalBlock, 0) !=
+            cudaSuccess)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
 template <typename T, int K>
 cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, void *vn,
                         int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
@@ -184,6 +222,11 @@ cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, vo
     constexpr int H = (K + V - 1) / V;
     constexpr int OUTW = (32 - 2 * H) * V;
     const int bands = (int)((nm + OUTW - 1) / OUTW);
+    if (rows <= 0) {
+        const int bps = reaction == RDCNN_REACTION_FHN ? temporal_blocks_per_sm<T, K, RX_FHN>()
+                                                       : temporal_blocks_per_sm<T, K, RX_NONE>();
+        rows = auto_rows_temporal(K, nn, nm, bands, bps, kTemporalBlock / 32);
+    }
     const int strips = (int)((nn + rows - 1) / rows);
     const int64_t nwarps = (int64_t)bands * strips;
     const int wpb = kTemporalBlock / 32;
@@ -279,20 +322,25 @@ cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, i
     return cudaGetLastError();
 }
 
-int default_k(int dtype) { return dtype == RDCNN_F64 ? 4 : 8; }
+// Temporal depth by grid size, from a launch-shape sweep on GB300 (FP32,
+// square grids): 128^2-256^2 k=4, 512^2 k=6, 1024^2 k=4, >= 2048^2 k=8.
+// Small grids are latency/launch bound, where fewer, shallower stages in
+// more warps win; large grids are FP32-pipe bound, where depth amortises
+// the halo.  FP64 is capped at its maximum depth.
+int default_k(int dtype, int64_t nn, int64_t nm) {
+    const int64_t cells = nn * nm;
+    int k;
+    if (cells >= (int64_t(1) << 21)) k = 8;
+    else if (cells >= (int64_t(1) << 19)) k = 4;
+    else if (cells >= (int64_t(1) << 17)) k = 6;
+    else k = 4;
+    return std::min(k, max_k(dtype));
+}
 
-// Launch shapes measured on GB300 at 4096^2 FP32: the single-step kernel is
-// fastest with short strips (more warps in flight), the temporal kernel with
-// strips long enough to amortise the 2k-row pipeline fill.
+// The single-step kernel is fastest with short strips (more warps in flight).
 int default_rows_step1(int dtype, int64_t nn, int64_t nm) {
     (void)dtype; (void)nn; (void)nm;
     return 4;
-}
-
-int default_rows_temporal(int dtype, int k, int64_t nn, int64_t nm) {
-    (void)dtype; (void)nm;
-    const int r = nn >= 2048 ? 128 : (nn >= 512 ? 64 : 32);
-    return std::max(r, 4 * k);
 }
 
 }  // namespace rdk

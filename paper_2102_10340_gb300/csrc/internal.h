@@ -54,9 +54,9 @@ cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v
 cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
                         cudaStream_t s);
 
-// Default launch shapes (rows per warp strip) and temporal depth.
+// Default launch shapes.  launch_temporal picks its rows per warp strip
+// itself when given rows <= 0.
 int default_rows_step1(int dtype, int64_t nn, int64_t nm);
-int default_rows_temporal(int dtype, int k, int64_t nn, int64_t nm);
-int default_k(int dtype);
+int default_k(int dtype, int64_t nn, int64_t nm);
 
 }  // namespace rdk

@@ -84,7 +84,7 @@ int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, i
                          "(at most %zu cells of this dtype)",
                          (long long)nn, (long long)nm, 2 * plane, kStaticScratchBytes,
                          kStaticScratchBytes / 2 / elem_size(dtype));
-    if (k == 0) k = default_k(dtype);
+    if (k == 0) k = default_k(dtype, nn, nm);
     if (k < 1 || k > max_k(dtype)) return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(dtype));
     if (T == 0) return pc;
 
@@ -100,8 +100,7 @@ int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, i
     for (int64_t left = T; left > 0;) {
         const int kk = vec ? (int)(left < k ? left : k) : 1;
         const cudaError_t e =
-            vec ? launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, *p,
-                                  default_rows_temporal(dtype, kk, nn, nm), s)
+            vec ? launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, *p, 0, s)
                 : launch_generic(dtype, reaction, cu, cv, nu, nv, nn, nm, *p, s);
         if (e != cudaSuccess) return cuda_error(e, "static-scratch step launch");
         const void *tu = cu, *tv = cv;
