@@ -9,33 +9,38 @@
 //   dL/dDu += dt sum lu Lap(u)     dL/dDv += dt sum lv Lap(v)
 //   dL/dc  += dt sum lu u          dL/da  += dt sum lv (-eps)
 //   dL/db  += dt sum lv eps v      dL/deps += dt sum lv (-(u - b v + a))
-// with (u, v) the state before the step.
+// with (u, v) the state before the step.  Because the Laplacian is symmetric,
+// sum lu Lap(u) = sum u Lap(lu): the Du / Dv terms reuse the co-state
+// neighbour sums the update forms anyway, and the state is needed only at
+// the centre cell.
 //
-// Driver: forward sweep storing n_ck checkpoints (every S = ceil(T/n_ck)
-// steps), then segments in reverse: rebuild the S states of the segment with
-// single-step launches, then walk them backwards with k_adjoint_step.  Each
-// warp of k_adjoint_step owns the same cells at every step and adds its FP64
-// partial sums to its own slot, so the gradient is deterministic.
+// Driver: a forward sweep stores n_ck checkpoints (every S = ceil(T/n_ck)
+// steps).  Segments are then processed last to first: k_forward_all rebuilds
+// the segment's states K per launch (every stage of the temporal pipeline is
+// stored), and k_adjoint_pipe walks them backwards K steps per launch with
+// the same register pipeline running the co-state update.  Each warp owns
+// the same cells at every launch and adds its sums to its own FP64 slot, so
+// the gradient is deterministic.
 #include <algorithm>
 #include <cmath>
-#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
+#include "temporal.cuh"
 
 namespace rdk {
 
 namespace {
 
-constexpr int kAdjBlock = 256;
+constexpr int kPipeBlock = 32 * kTemporalWarps;
 
 // Coefficients of the reverse step, arranged like the forward cell update
 // (the -4 centre weight folded in): cm4 = c - 4 Du, ebm4 = eps b - 4 Dv;
 // with no reaction cm4 = -4 Du, ebm4 = -4 Dv and the rest is unused.
-// a, b, eps (FP64) enter only the gradient sums.
+// a, eps (FP64) enter only the final scaling of the gradient sums.
 template <typename T> struct AdjCoef {
-    T dt, Du, Dv, cm4, meps, ebm4;
-    double a, b, eps;
+    T dt, Du, Dv, cm4, meps, ebm4, mb;
+    double a, eps;
 };
 
 template <typename T>
@@ -46,92 +51,75 @@ AdjCoef<T> make_adj_coef(const rdcnn_params &p, int reaction) {
     q.cm4 = T((fhn ? p.c : 0.0) - 4.0 * p.Du);
     q.meps = T(fhn ? -p.eps : 0.0);
     q.ebm4 = T((fhn ? p.eps * p.b : 0.0) - 4.0 * p.Dv);
-    q.a = p.a; q.b = p.b; q.eps = p.eps;
+    q.mb = T(-p.b);
+    q.a = p.a; q.eps = p.eps;
     return q;
 }
 
-__device__ __forceinline__ double warp_sum(double x) {
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T x) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    for (int o = 16; o > 0; o >>= 1) x = add_rn(x, __shfl_xor_sync(kFull, x, o));
     return x;
 }
 
-// One reverse step for a (band, strip) of rows.  The co-state (lu, lv) is
-// streamed with a 3-row window plus one prefetched row (Slice<T>.u = lu,
-// .v = lv); the state (u, v) at the same time level is needed only at the
-// centre cell.  The Du / Dv gradient terms use the symmetry of the periodic
-// Laplacian, sum_k lu_k Lap(u)_k = sum_k u_k Lap(lu)_k, so they reuse the
-// co-state neighbour sums the update forms anyway.  Per-row sums of the six
-// gene terms are formed in T and accumulated in FP64.
-template <typename T, int RX>
-__global__ void __launch_bounds__(kAdjBlock)
-k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ lu,
-               const T *__restrict__ lv, T *__restrict__ lun, T *__restrict__ lvn,
-               double *__restrict__ partial, int nn, int nm, int bands, int nwarps, int rows,
-               AdjCoef<T> p) {
-    constexpr int V = Vec<T>::N;
-    const int lane = threadIdx.x & 31;
-    const int wid = blockIdx.x * (kAdjBlock / 32) + (threadIdx.x >> 5);
-    if (wid >= nwarps) return;
-    const int band = wid % bands;
-    const int strip = wid / bands;
-    const int col = band * 32 * V + lane * V;
-    const bool active = col < nm;
-    const int colw = (col == 0) ? nm - 1 : col - 1;
-    const int cole = (col + V >= nm) ? 0 : col + V;
-    const bool edge_w = (lane == 0);
-    const bool edge_e = active && (lane == 31 || col + V >= nm);
-    const int r0 = strip * rows;
-    const int r1 = min(r0 + rows, nn);
+// Reverse policy for the K-stage pipeline.  The pipeline streams the
+// co-state (Slice.u = lu, Slice.v = lv, time t_hi first); stage s produces
+// the co-state at time t_hi - s - 1 from the one at t_hi - s, using the state
+// at time t_hi - s - 1 (state.u[s], state.v[s]) at the centre cell.  State
+// rows travel through a per-warp shared-memory ring (one per stage) filled by
+// cp.async in the same commit groups as the co-state rows, kRing - 1 beats
+// ahead of use.  The six gene sums run in T over the owned cells and reach
+// FP64 once per warp (FP64 arithmetic is slow here).
+template <typename T, int K, int RX>
+struct ReversePolicy {
+    typedef typename Vec<T>::type VT;
+    const AdjCoef<T> &p;
+    const StripGeom &geo;
+    const StagePlanes<T> &state;
+    T *__restrict__ lun;
+    T *__restrict__ lvn;
+    int nn, nm;
+    VT (*aux)[kRing][2][32];  // [stage][slot][field][lane]
+    int gi[K];                // next state row to copy, per stage
+    T rg[6];                  // sums: u Lap(lu), v Lap(lv), lv, lv v, lv (u - b v), lu u
 
-    Slice<T> nor, cen, sou, pre, st, st_pre;  // co-state rows r-1, r, r+1, r+2; state rows r, r+1
-    zero_slice(nor); zero_slice(cen); zero_slice(sou); zero_slice(pre); zero_slice(st); zero_slice(st_pre);
-    T cw_u = 0, ce_u = 0, cw_v = 0, ce_v = 0, sw_u = 0, se_u = 0, sw_v = 0, se_v = 0;
-    T pw_u = 0, pe_u = 0, pw_v = 0, pe_v = 0;
-    const int rn = (r0 == 0) ? nn - 1 : r0 - 1;
-    int rs = (r0 + 1 == nn) ? 0 : r0 + 1;
-    if (active) {
-        load_slice(nor, lu, lv, (int64_t)rn * nm + col);
-        load_slice(cen, lu, lv, (int64_t)r0 * nm + col);
-        load_slice(sou, lu, lv, (int64_t)rs * nm + col);
-        load_slice(st, u, v, (int64_t)r0 * nm + col);
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) rg[q] = T(0);
+        // stage s at beat m reads input-row index q = m - s - 1
+#pragma unroll
+        for (int s = 0; s < K; ++s) gi[s] = wrap_row((int64_t)geo.r0 - K - s - 1, nn);
     }
-    if (edge_w) {
-        cw_u = __ldg(lu + (int64_t)r0 * nm + colw); cw_v = __ldg(lv + (int64_t)r0 * nm + colw);
-        sw_u = __ldg(lu + (int64_t)rs * nm + colw); sw_v = __ldg(lv + (int64_t)rs * nm + colw);
-    }
-    if (edge_e) {
-        ce_u = __ldg(lu + (int64_t)r0 * nm + cole); ce_v = __ldg(lv + (int64_t)r0 * nm + cole);
-        se_u = __ldg(lu + (int64_t)rs * nm + cole); se_v = __ldg(lv + (int64_t)rs * nm + cole);
-    }
-    double g[6] = {0, 0, 0, 0, 0, 0};
-    for (int r = r0; r < r1; ++r) {
-        const bool more = (r + 1 < r1);
-        const int rp = (rs + 1 == nn) ? 0 : rs + 1;
-        if (more) {
-            if (active) {
-                load_slice(pre, lu, lv, (int64_t)rp * nm + col);
-                load_slice(st_pre, u, v, (int64_t)rs * nm + col);
-            }
-            if (edge_w) { pw_u = __ldg(lu + (int64_t)rp * nm + colw); pw_v = __ldg(lv + (int64_t)rp * nm + colw); }
-            if (edge_e) { pe_u = __ldg(lu + (int64_t)rp * nm + cole); pe_v = __ldg(lv + (int64_t)rp * nm + cole); }
+    __device__ __forceinline__ void issue(int j) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            const int64_t off = (int64_t)gi[s] * nm + geo.lc;
+            cp_async16(&aux[s][j % kRing][0][lane], state.u[s] + off);
+            cp_async16(&aux[s][j % kRing][1][lane], state.v[s] + off);
+            gi[s] = (gi[s] + 1 == nn) ? 0 : gi[s] + 1;
         }
-        T wu = __shfl_up_sync(kFull, cen.u[V - 1], 1);
-        T eu = __shfl_down_sync(kFull, cen.u[0], 1);
-        T wv = __shfl_up_sync(kFull, cen.v[V - 1], 1);
-        T ev = __shfl_down_sync(kFull, cen.v[0], 1);
-        if (edge_w) { wu = cw_u; wv = cw_v; }
-        if (edge_e) { eu = ce_u; ev = ce_v; }
-        T ou[V], ov[V];
-        T rg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    }
+    __device__ __forceinline__ void begin_beat(int) {}
+    __device__ __forceinline__ void stage(int s, const Slice<T> &A, const Slice<T> &B, const Slice<T> &C,
+                                          T wu, T eu, T wv, T ev, int q, Slice<T> &out) {
+        constexpr int V = Vec<T>::N;
+        const bool own = (q >= K) && (q < K + geo.nout) && geo.st_lane;
+        const int lane = threadIdx.x & 31;
+        const int slot = (q + s + 1) % kRing;  // beat m = q + s + 1
+        const VT su4 = aux[s][slot][0][lane];
+        const VT sv4 = aux[s][slot][1][lane];
+        const T *stu = reinterpret_cast<const T *>(&su4);
+        const T *stv = reinterpret_cast<const T *>(&sv4);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            const T luc = cen.u[e], lvc = cen.v[e];
-            const T su = add_rn(add_rn(nor.u[e], sou.u[e]), add_rn(e == 0 ? wu : cen.u[e - 1],
-                                                                   e == V - 1 ? eu : cen.u[e + 1]));
-            const T sv = add_rn(add_rn(nor.v[e], sou.v[e]), add_rn(e == 0 ? wv : cen.v[e - 1],
-                                                                   e == V - 1 ? ev : cen.v[e + 1]));
-            const T uc = st.u[e], vc = st.v[e];
+            const T luc = B.u[e], lvc = B.v[e];
+            const T su = add_rn(add_rn(A.u[e], C.u[e]), add_rn(e == 0 ? wu : B.u[e - 1],
+                                                               e == V - 1 ? eu : B.u[e + 1]));
+            const T sv = add_rn(add_rn(A.v[e], C.v[e]), add_rn(e == 0 ? wv : B.v[e - 1],
+                                                               e == V - 1 ? ev : B.v[e + 1]));
+            const T uc = stu[e], vc = stv[e];
             // co-state update with the centre term folded in, like the forward:
             //   lu + dt [ Du s(lu) + (c - 4 Du - u^2) lu - eps lv ]
             //   lv + dt [ Dv s(lv) + (eps b - 4 Dv) lv - lu ]
@@ -143,40 +131,76 @@ k_adjoint_step(const T *__restrict__ u, const T *__restrict__ v, const T *__rest
                 ru = mul_rn(p.cm4, luc);
                 rv = mul_rn(p.ebm4, lvc);
             }
-            ou[e] = fma_rn(p.dt, fma_rn(p.Du, su, ru), luc);
-            ov[e] = fma_rn(p.dt, fma_rn(p.Dv, sv, rv), lvc);
-            rg[0] = fma_rn(uc, fma_rn(T(-4), luc, su), rg[0]);     // u Lap(lu)
-            rg[1] = fma_rn(vc, fma_rn(T(-4), lvc, sv), rg[1]);     // v Lap(lv)
-            if (RX == RX_FHN) {
-                rg[2] = add_rn(rg[2], lvc);                        // lv        (x -eps)
-                rg[3] = fma_rn(lvc, vc, rg[3]);                    // lv v      (x eps)
-                rg[4] = fma_rn(lvc, fma_rn(T(-p.b), vc, uc), rg[4]);  // lv (u - b v)
-                rg[5] = fma_rn(luc, uc, rg[5]);                    // lu u
+            out.u[e] = fma_rn(p.dt, fma_rn(p.Du, su, ru), luc);
+            out.v[e] = fma_rn(p.dt, fma_rn(p.Dv, sv, rv), lvc);
+            if (own) {
+                rg[0] = fma_rn(uc, fma_rn(T(-4), luc, su), rg[0]);     // u Lap(lu)
+                rg[1] = fma_rn(vc, fma_rn(T(-4), lvc, sv), rg[1]);     // v Lap(lv)
+                if (RX == RX_FHN) {
+                    rg[2] = add_rn(rg[2], lvc);                        // lv        (x -eps)
+                    rg[3] = fma_rn(lvc, vc, rg[3]);                    // lv v      (x eps)
+                    rg[4] = fma_rn(lvc, fma_rn(p.mb, vc, uc), rg[4]);  // lv (u - b v)
+                    rg[5] = fma_rn(luc, uc, rg[5]);                    // lu u
+                }
             }
         }
-        if (active) {
-            const int64_t off = (int64_t)r * nm + col;
-            store_vec<T>(lun + off, ou);
-            store_vec<T>(lvn + off, ov);
-            g[0] += (double)rg[0];
-            g[1] += (double)rg[1];
-            if (RX == RX_FHN) {
-                g[2] -= p.eps * (double)rg[2];
-                g[3] += p.eps * (double)rg[3];
-                g[4] -= (double)rg[4] + p.a * (double)rg[2];
-                g[5] += (double)rg[5];
-            }
-        }
-        nor = cen; cen = sou; sou = pre; st = st_pre;
-        cw_u = sw_u; ce_u = se_u; cw_v = sw_v; ce_v = se_v;
-        sw_u = pw_u; se_u = pe_u; sw_v = pw_v; se_v = pe_v;
-        rs = rp;
     }
+    __device__ __forceinline__ void finish(int q, const Slice<T> &out) {
+        const int orow = q - K;
+        if (orow >= 0 && geo.st_lane) {
+            const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
+            store_vec<T>(lun + off, out.u);
+            store_vec<T>(lvn + off, out.v);
+        }
+    }
+    __device__ __forceinline__ void flush(double *__restrict__ slot) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const double s = warp_sum(g[q]);
-        if (lane == 0) partial[(int64_t)wid * 6 + q] += s;
+        for (int q = 0; q < 6; ++q) rg[q] = warp_sum_t(rg[q]);
+        if ((threadIdx.x & 31) == 0) {
+            slot[0] += (double)rg[0];
+            slot[1] += (double)rg[1];
+            if (RX == RX_FHN) {
+                slot[2] -= p.eps * (double)rg[2];
+                slot[3] += p.eps * (double)rg[3];
+                slot[4] -= (double)rg[4] + p.a * (double)rg[2];
+                slot[5] += (double)rg[5];
+            }
+        }
     }
+};
+
+// K reverse steps: co-state (lu, lv) at t_hi -> (lun, lvn) at t_hi - K, with
+// state.u[s], state.v[s] = state at t_hi - s - 1.  H: halo lanes (fixed per
+// call sequence so every launch has the same warp -> cells map).
+template <typename T, int K, int H, int RX>
+__global__ void __launch_bounds__(kPipeBlock)
+k_adjoint_pipe(const T *__restrict__ lu, const T *__restrict__ lv, T *__restrict__ lun,
+               T *__restrict__ lvn, StagePlanes<T> state, double *__restrict__ partial, int nn,
+               int nm, int bands, int nwarps, int rows, AdjCoef<T> p) {
+    const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
+    if (wid >= nwarps) return;
+    const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
+    typedef typename Vec<T>::type VT;
+    // state rings in dynamic shared memory: [warp][stage][slot][field][lane]
+    extern __shared__ __align__(16) unsigned char adj_dyn_smem[];
+    VT(*aux_mem)[K][kRing][2][32] = reinterpret_cast<VT(*)[K][kRing][2][32]>(adj_dyn_smem);
+    ReversePolicy<T, K, RX> pol{p, geo, state, lun, lvn, nn, nm, aux_mem[(threadIdx.x >> 5) % kTemporalWarps]};
+    pol.init();
+    pipeline_strip<T, K>(geo, lu, lv, nn, nm, pol);
+    pol.flush(partial + (int64_t)wid * 6);
+}
+
+// K forward steps from (u, v), storing the state after every step s+1 into
+// planes.u[s], planes.v[s] (the states a reverse sweep reads).
+template <typename T, int K, int H, int RX>
+__global__ void __launch_bounds__(kPipeBlock)
+k_forward_all(const T *__restrict__ u, const T *__restrict__ v, StagePlanes<T> planes, int nn,
+              int nm, int bands, int nwarps, int rows, Coef<T> p) {
+    const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
+    if (wid >= nwarps) return;
+    const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
+    ForwardAllPolicy<T, K, RX> pol{p, geo, planes, nm};
+    pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
 }
 
 // Sum per-warp partials (fixed order), scale by dt: out[q] = dt * sum_w partial[w][q].
@@ -197,43 +221,106 @@ k_reduce_partials(const double *__restrict__ partial, int nwarps, double dt, dou
     }
 }
 
-// Rows per warp: enough warps to fill the GPU (~2048), at most 16 rows.
-int adj_rows(int64_t nn, int bands) {
-    const int64_t r = nn * bands / 2048;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(16, r));
-}
+// Depth of the recompute / reverse launches: 4 steps with one halo lane for
+// FP32, 2 steps (one lane of two doubles) for FP64.
+inline int adj_depth(int dtype) { return dtype == RDCNN_F64 ? 2 : 4; }
 
-struct AdjShape {
+struct PipeShape {
     int bands, strips, nwarps, rows;
 };
 
-AdjShape adj_shape(int dtype, int64_t nn, int64_t nm) {
-    AdjShape s;
+// One warp -> cells map for every recompute / reverse launch of a call.
+PipeShape pipe_shape(int dtype, int64_t nn, int64_t nm) {
     const int V = vec_width(dtype);
-    s.bands = (int)((nm + 32 * V - 1) / (32 * V));
-    s.rows = adj_rows(nn, s.bands);
+    const int outw = (32 - 2) * V;  // one halo lane per side
+    PipeShape s;
+    const int64_t cells = nn * nm;
+    s.rows = cells < (int64_t(1) << 17) ? 4 : cells < (int64_t(1) << 19) ? 8 : cells < (int64_t(1) << 22) ? 16 : 64;
+    s.bands = (int)((nm + outw - 1) / outw);
     s.strips = (int)((nn + s.rows - 1) / s.rows);
     s.nwarps = s.bands * s.strips;
     return s;
 }
 
-template <typename T>
-cudaError_t adjoint_step_t(int reaction, const void *u, const void *v, const void *lu,
-                           const void *lv, void *lun, void *lvn, double *partial, int64_t nn,
-                           int64_t nm, const rdcnn_params &p, const AdjShape &sh, cudaStream_t s) {
-    const int wpb = kAdjBlock / 32;
-    const unsigned grid = (unsigned)((sh.nwarps + wpb - 1) / wpb);
+// Dynamic shared memory of k_adjoint_pipe<T, K>: the per-stage state rings.
+template <typename T, int K>
+constexpr size_t pipe_smem_bytes() {
+    return (size_t)kTemporalWarps * K * kRing * 2 * 32 * sizeof(typename Vec<T>::type);
+}
+
+// Opt the kernel in to its dynamic shared memory (above the 48 KB default), once.
+template <typename T, int K, int RX>
+cudaError_t pipe_smem_optin() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaErrorNotReady)
+        done = cudaFuncSetAttribute(k_adjoint_pipe<T, K, 1, RX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pipe_smem_bytes<T, K>());
+    return done;
+}
+
+template <typename T, int K>
+cudaError_t reverse_launch_k(int reaction, const void *lu, const void *lv, void *lun, void *lvn,
+                             const StagePlanes<T> &st, double *partial, int64_t nn, int64_t nm,
+                             const PipeShape &sh, const rdcnn_params &p, cudaStream_t s) {
+    const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const AdjCoef<T> c = make_adj_coef<T>(p, reaction);
+    const size_t smem = pipe_smem_bytes<T, K>();
+    const cudaError_t oe = reaction == RDCNN_REACTION_FHN ? pipe_smem_optin<T, K, RX_FHN>()
+                                                          : pipe_smem_optin<T, K, RX_NONE>();
+    if (oe != cudaSuccess) return oe;
     if (reaction == RDCNN_REACTION_FHN)
-        k_adjoint_step<T, RX_FHN><<<grid, kAdjBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, partial,
-            (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
+        k_adjoint_pipe<T, K, 1, RX_FHN><<<grid, kPipeBlock, smem, s>>>(
+            (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, st, partial, (int)nn, (int)nm,
+            sh.bands, sh.nwarps, sh.rows, c);
     else
-        k_adjoint_step<T, RX_NONE><<<grid, kAdjBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, partial,
-            (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
+        k_adjoint_pipe<T, K, 1, RX_NONE><<<grid, kPipeBlock, smem, s>>>(
+            (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, st, partial, (int)nn, (int)nm,
+            sh.bands, sh.nwarps, sh.rows, c);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <typename T, int K>
+cudaError_t forward_all_launch_k(int reaction, const void *u, const void *v, const StagePlanes<T> &pl,
+                                 int64_t nn, int64_t nm, const PipeShape &sh, const rdcnn_params &p,
+                                 cudaStream_t s) {
+    const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
+    const Coef<T> c = make_coef<T>(p, reaction);
+    if (reaction == RDCNN_REACTION_FHN)
+        k_forward_all<T, K, 1, RX_FHN><<<grid, kPipeBlock, 0, s>>>(
+            (const T *)u, (const T *)v, pl, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
+    else
+        k_forward_all<T, K, 1, RX_NONE><<<grid, kPipeBlock, 0, s>>>(
+            (const T *)u, (const T *)v, pl, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Depth dispatch (depth <= V keeps one halo lane): F32 1..4, F64 1..2.
+template <typename T>
+cudaError_t reverse_launch(int reaction, int k, const void *lu, const void *lv, void *lun, void *lvn,
+                           const StagePlanes<T> &st, double *partial, int64_t nn, int64_t nm,
+                           const PipeShape &sh, const rdcnn_params &p, cudaStream_t s) {
+    switch (k) {
+        case 1: return reverse_launch_k<T, 1>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
+        case 2: return reverse_launch_k<T, 2>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
+        case 3: if constexpr (Vec<T>::N >= 3) return reverse_launch_k<T, 3>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
+        case 4: if constexpr (Vec<T>::N >= 4) return reverse_launch_k<T, 4>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t forward_all_launch(int reaction, int k, const void *u, const void *v, const StagePlanes<T> &pl,
+                               int64_t nn, int64_t nm, const PipeShape &sh, const rdcnn_params &p,
+                               cudaStream_t s) {
+    switch (k) {
+        case 1: return forward_all_launch_k<T, 1>(reaction, u, v, pl, nn, nm, sh, p, s);
+        case 2: return forward_all_launch_k<T, 2>(reaction, u, v, pl, nn, nm, sh, p, s);
+        case 3: if constexpr (Vec<T>::N >= 3) return forward_all_launch_k<T, 3>(reaction, u, v, pl, nn, nm, sh, p, s); break;
+        case 4: if constexpr (Vec<T>::N >= 4) return forward_all_launch_k<T, 4>(reaction, u, v, pl, nn, nm, sh, p, s); break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 struct AdjLayout {
@@ -249,7 +336,7 @@ AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck) 
     L.nseg = (std::max<int64_t>(T, 1) + L.S - 1) / L.S;
     L.nslots = std::max<int64_t>(L.S, 2);
     L.plane = (((size_t)nn * nm * elem_size(dtype)) + 255) & ~(size_t)255;
-    const AdjShape sh = adj_shape(dtype, nn, nm);
+    const PipeShape sh = pipe_shape(dtype, nn, nm);
     L.ck_off = 0;
     L.seg_off = L.ck_off + (size_t)L.nseg * 2 * L.plane;
     L.lam_off = L.seg_off + (size_t)L.nslots * 2 * L.plane;
@@ -257,6 +344,83 @@ AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck) 
     L.out_off = L.part_off + (((size_t)sh.nwarps * 6 * sizeof(double) + 255) & ~(size_t)255);
     L.total = L.out_off + 256;
     return L;
+}
+
+template <typename T>
+int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, cudaStream_t s,
+              int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T, const void *dLdv_T,
+              const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
+    const size_t bytes = (size_t)nn * nm * sizeof(T);
+    auto ck_u = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i) * L.plane); };
+    auto ck_v = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i + 1) * L.plane); };
+    auto seg_u = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * i) * L.plane); };
+    auto seg_v = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * i + 1) * L.plane); };
+    T *lam_u[2] = {(T *)(ws + L.lam_off), (T *)(ws + L.lam_off + 2 * L.plane)};
+    T *lam_v[2] = {(T *)(ws + L.lam_off + L.plane), (T *)(ws + L.lam_off + 3 * L.plane)};
+    double *partial = (double *)(ws + L.part_off);
+    double *gout = (double *)(ws + L.out_off);
+    const PipeShape sh = pipe_shape(dtype, nn, nm);
+    const int kf = default_k(dtype, nn, nm);  // depth of the checkpoint sweep
+    const int ka = adj_depth(dtype);          // depth of recompute / reverse launches
+
+    cudaError_t e = cudaMemcpyAsync(lam_u[0], dLdu_T, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lam_v[0], dLdv_T, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_u(0), u0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_v(0), v0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, (size_t)sh.nwarps * 6 * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint setup copies");
+
+    // forward sweep: checkpoint i = state at step i*S
+    for (int64_t i = 0; i + 1 < L.nseg && nsteps > 0; ++i) {
+        const int64_t len = L.S;
+        const int64_t nl = (len + kf - 1) / kf;
+        const void *cu = ck_u(i), *cv = ck_v(i);
+        for (int64_t j = 0; j < nl; ++j) {
+            const int kk = (int)std::min<int64_t>(kf, len - j * kf);
+            void *nu = (j == nl - 1) ? (void *)ck_u(i + 1) : (void *)seg_u(j % 2);
+            void *nv = (j == nl - 1) ? (void *)ck_v(i + 1) : (void *)seg_v(j % 2);
+            e = launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
+            if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
+            cu = nu; cv = nv;
+        }
+    }
+    // segments last to first: rebuild the states, then sweep the co-state back
+    int cur = 0;
+    for (int64_t sg = L.nseg - 1; sg >= 0 && nsteps > 0; --sg) {
+        const int64_t len = std::min<int64_t>(L.S, nsteps - sg * L.S);
+        auto state_u = [&](int64_t q) { return q == 0 ? ck_u(sg) : seg_u(q); };
+        auto state_v = [&](int64_t q) { return q == 0 ? ck_v(sg) : seg_v(q); };
+        for (int64_t q = 0; q + 1 < len;) {
+            const int kk = (int)std::min<int64_t>(ka, len - 1 - q);
+            StagePlanes<T> pl{};
+            for (int j = 0; j < kk; ++j) { pl.u[j] = seg_u(q + 1 + j); pl.v[j] = seg_v(q + 1 + j); }
+            e = forward_all_launch<T>(reaction, kk, state_u(q), state_v(q), pl, nn, nm, sh, p, s);
+            if (e != cudaSuccess) return cuda_error(e, "adjoint recompute");
+            q += kk;
+        }
+        for (int64_t qh = len; qh > 0;) {
+            const int kk = (int)std::min<int64_t>(ka, qh);
+            StagePlanes<T> st{};
+            for (int j = 0; j < kk; ++j) { st.u[j] = state_u(qh - 1 - j); st.v[j] = state_v(qh - 1 - j); }
+            e = reverse_launch<T>(reaction, kk, lam_u[cur], lam_v[cur], lam_u[cur ^ 1], lam_v[cur ^ 1], st,
+                                  partial, nn, nm, sh, p, s);
+            if (e != cudaSuccess) return cuda_error(e, "adjoint reverse step");
+            cur ^= 1;
+            qh -= kk;
+        }
+    }
+    k_reduce_partials<<<1, 256, 0, s>>>(partial, sh.nwarps, p.dt, gout);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "gradient reduction");
+    e = cudaMemcpyAsync(dLdu0, lam_u[cur], bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dLdv0, lam_v[cur], bytes, cudaMemcpyDeviceToDevice, s);
+    double hg[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hg, gout, sizeof(hg), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint results");
+    for (int q = 0; q < 6; ++q) grad[q] = hg[q];
+    return RDCNN_OK;
 }
 
 }  // namespace
@@ -295,78 +459,11 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints);
     if (workspace_bytes < L.total)
         return set_error(RDCNN_ESPACE, "adjoint workspace has %zu bytes, need %zu", workspace_bytes, L.total);
-    const size_t bytes = (size_t)nn * nm * elem_size(dtype);
-    char *ws = (char *)workspace;
-    auto ck_u = [&](int64_t i) { return (void *)(ws + L.ck_off + (size_t)(2 * i) * L.plane); };
-    auto ck_v = [&](int64_t i) { return (void *)(ws + L.ck_off + (size_t)(2 * i + 1) * L.plane); };
-    auto seg_u = [&](int64_t i) { return (void *)(ws + L.seg_off + (size_t)(2 * i) * L.plane); };
-    auto seg_v = [&](int64_t i) { return (void *)(ws + L.seg_off + (size_t)(2 * i + 1) * L.plane); };
-    void *lam_u[2] = {ws + L.lam_off, ws + L.lam_off + 2 * L.plane};
-    void *lam_v[2] = {ws + L.lam_off + L.plane, ws + L.lam_off + 3 * L.plane};
-    double *partial = (double *)(ws + L.part_off);
-    double *gout = (double *)(ws + L.out_off);
-    const AdjShape sh = adj_shape(dtype, nn, nm);
-    const int k = default_k(dtype, nn, nm);
-    const int rows_t = 0;  // chosen by the launcher
-    const int rows_1 = default_rows_step1(dtype, nn, nm);
-
-    cudaError_t e = cudaMemcpyAsync(lam_u[0], dLdu_T, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(lam_v[0], dLdv_T, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_u(0), u0, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_v(0), v0, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, (size_t)sh.nwarps * 6 * sizeof(double), s);
-    if (e != cudaSuccess) return cuda_error(e, "adjoint setup copies");
-
-    // forward sweep: checkpoint i = state at step i*S
-    for (int64_t i = 0; i + 1 < L.nseg && T > 0; ++i) {
-        const int64_t len = L.S;
-        const int64_t nl = (len + k - 1) / k;
-        const void *cu = ck_u(i), *cv = ck_v(i);
-        for (int64_t j = 0; j < nl; ++j) {
-            const int kk = (int)std::min<int64_t>(k, len - j * k);
-            void *nu = (j == nl - 1) ? ck_u(i + 1) : seg_u(j % 2);
-            void *nv = (j == nl - 1) ? ck_v(i + 1) : seg_v(j % 2);
-            e = launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, p, rows_t, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
-            cu = nu; cv = nv;
-        }
-    }
-    // reverse sweep over segments
-    int cur = 0;
-    for (int64_t sg = L.nseg - 1; sg >= 0 && T > 0; --sg) {
-        const int64_t t0 = sg * L.S;
-        const int64_t len = std::min<int64_t>(L.S, T - t0);
-        for (int64_t q = 1; q < len; ++q) {
-            const void *pu = (q == 1) ? ck_u(sg) : seg_u(q - 1);
-            const void *pv = (q == 1) ? ck_v(sg) : seg_v(q - 1);
-            e = launch_step1(dtype, reaction, pu, pv, seg_u(q), seg_v(q), nn, nm, p, rows_1, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint recompute");
-        }
-        for (int64_t q = len - 1; q >= 0; --q) {
-            const void *su = (q == 0) ? ck_u(sg) : seg_u(q);
-            const void *sv = (q == 0) ? ck_v(sg) : seg_v(q);
-            if (dtype == RDCNN_F64)
-                e = adjoint_step_t<double>(reaction, su, sv, lam_u[cur], lam_v[cur], lam_u[cur ^ 1],
-                                           lam_v[cur ^ 1], partial, nn, nm, p, sh, s);
-            else
-                e = adjoint_step_t<float>(reaction, su, sv, lam_u[cur], lam_v[cur], lam_u[cur ^ 1],
-                                          lam_v[cur ^ 1], partial, nn, nm, p, sh, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint step");
-            cur ^= 1;
-        }
-    }
-    k_reduce_partials<<<1, 256, 0, s>>>(partial, sh.nwarps, p.dt, gout);
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "gradient reduction");
-    e = cudaMemcpyAsync(dLdu0, lam_u[cur], bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dLdv0, lam_v[cur], bytes, cudaMemcpyDeviceToDevice, s);
-    double hg[6];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hg, gout, sizeof(hg), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_error(e, "adjoint results");
-    for (int q = 0; q < 6; ++q) grad[q] = hg[q];
-    return RDCNN_OK;
+    if (dtype == RDCNN_F64)
+        return adjoint_t<double>(nn, nm, p, dtype, reaction, s, T, u0, v0, dLdu_T, dLdv_T, L,
+                                 (char *)workspace, dLdu0, dLdv0, grad);
+    return adjoint_t<float>(nn, nm, p, dtype, reaction, s, T, u0, v0, dLdu_T, dLdv_T, L,
+                            (char *)workspace, dLdu0, dLdv0, grad);
 }
 
 }  // extern "C"

@@ -62,16 +62,24 @@ __device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<T> &
 }
 
 // One pipeline beat: take input row m of the strip from the ring (issuing the
-// copy of row m + kRing - 1 first), advance every stage by one row, and store
-// the finished row (stage K) when it is inside the strip.  W[PH], W[PH+1] hold
-// the two older rows of each stage, W[PH+2] receives the newest, so a 3-beat
-// unroll rotates the windows without register moves.
-template <typename T, int K, int RX, int PH>
-__device__ __forceinline__ void temporal_beat(int m, int total, Slice<T> (&W)[3][K],
+// copy of row m + kRing - 1 first), advance every stage by one row, and hand
+// the finished row (stage K) to the policy.  W[PH], W[PH+1] hold the two older
+// rows of each stage, W[PH+2] receives the newest, so a 3-beat unroll rotates
+// the windows without register moves.
+//
+// The policy P supplies the per-stage arithmetic and the stores:
+//   P::issue(j)                          extra cp.async copies for beat j,
+//                                        committed with input row j
+//   P::begin_beat(m)                     before the stages of beat m
+//   P::stage<s>(A, B, C, wu, eu, wv, ev, q, out)
+//        stage s maps rows q-1 (A), q (B), q+1 (C) of its input to row q of
+//        its output (q = input-row index within the strip, see temporal_strip)
+//   P::finish(q, out)                    the row q leaving the last stage
+template <typename T, int K, int PH, class P>
+__device__ __forceinline__ void pipeline_beat(int m, int total, Slice<T> (&W)[3][K],
                                               const RowRing<T> &ring, int &g_issue, int nn, int nm,
                                               int lc, const T *__restrict__ u, const T *__restrict__ v,
-                                              T *__restrict__ un, T *__restrict__ vn,
-                                              int r0, int sc, bool st_lane, const Coef<T> &p) {
+                                              P &pol) {
     constexpr int V = Vec<T>::N;
     if (m >= total) return;
     // The slot written here was read in the previous beat, whose stage
@@ -79,11 +87,13 @@ __device__ __forceinline__ void temporal_beat(int m, int total, Slice<T> (&W)[3]
     if (m + kRing - 1 < total) {
         ring_issue(ring, m + kRing - 1, g_issue, nm, lc, u, v);
         g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+        pol.issue(m + kRing - 1);
     }
     cp_async_commit();
     cp_async_wait<kRing - 1>();  // the group holding row m is complete
     Slice<T> cur;
     ring_read(ring, m, cur);
+    pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
         Slice<T> &A = W[PH][s];
@@ -93,39 +103,45 @@ __device__ __forceinline__ void temporal_beat(int m, int total, Slice<T> (&W)[3]
         const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
         const T ev = __shfl_down_sync(kFull, B.v[0], 1);
         Slice<T> out;
-        slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
+        pol.stage(s, A, B, cur, wu, eu, wv, ev, m - s - 1, out);
         W[(PH + 2) % 3][s] = cur;
         cur = out;
     }
-    const int orow = m - 2 * K;
-    if (orow >= 0 && st_lane) {
-        const int64_t off = (int64_t)(r0 + orow) * nm + sc;
-        store_vec<T>(un + off, cur.u);
-        store_vec<T>(vn + off, cur.v);
-    }
+    pol.finish(m - K, cur);
 }
 
-// H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
-// needed only narrows the band), which lets a batched launch use one band
-// layout for launches of different depth.
-template <typename T, int K, int H, int RX>
-__device__ __forceinline__ void temporal_strip(int band, int strip, const T *__restrict__ u,
-                                               const T *__restrict__ v, T *__restrict__ un,
-                                               T *__restrict__ vn, int nn, int nm, int rows,
-                                               const Coef<T> &p) {
+// Geometry of one (band, strip) work item for depth K and halo H.
+// Input-row index q in 0 .. nout + 2K - 1 is global row r0 - K + q (wrapped);
+// the strip owns rows q in [K, K + nout) and lanes H .. 31-H whose column
+// sc = c0 + (lane - H) V is below NM.
+struct StripGeom {
+    int lc, sc, r0, nout, total;
+    bool st_lane;
+};
+
+template <typename T, int K, int H>
+__device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int nm, int rows) {
     constexpr int V = Vec<T>::N;
     static_assert(H * V >= K, "halo narrower than the temporal depth");
     static_assert(2 * H < 32, "halo wider than the warp");
     constexpr int OUTW = (32 - 2 * H) * V;
     const int lane = threadIdx.x & 31;
+    StripGeom g;
     const int c0 = band * OUTW;
-    const int lc = wrap_row((int64_t)c0 - H * V + lane * V, nm);  // V-aligned since nm % V == 0
-    const int sc = c0 + (lane - H) * V;
-    const bool st_lane = (lane >= H) && (lane < 32 - H) && (sc < nm);
-    const int r0 = strip * rows;
-    const int nout = min(rows, nn - r0);
-    const int total = nout + 2 * K;
+    g.lc = wrap_row((int64_t)c0 - H * V + lane * V, nm);  // V-aligned since nm % V == 0
+    g.sc = c0 + (lane - H) * V;
+    g.st_lane = (lane >= H) && (lane < 32 - H) && (g.sc < nm);
+    g.r0 = strip * rows;
+    g.nout = min(rows, nn - g.r0);
+    g.total = g.nout + 2 * K;
+    return g;
+}
 
+// Run one work item through the K-stage pipeline: input rows of (u, v) pass
+// through the stages; the policy decides what each stage computes and stores.
+template <typename T, int K, class P>
+__device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__restrict__ u,
+                                               const T *__restrict__ v, int nn, int nm, P &pol) {
     Slice<T> W[3][K];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -138,21 +154,89 @@ __device__ __forceinline__ void temporal_strip(int band, int strip, const T *__r
     ring.slot = ring_mem[(threadIdx.x >> 5) % kTemporalWarps];
 
     // prologue: rows 0 .. kRing-2 in flight, one commit group each
-    int g_issue = wrap_row((int64_t)r0 - K, nn);
+    int g_issue = wrap_row((int64_t)geo.r0 - K, nn);
 #pragma unroll
     for (int j = 0; j < kRing - 1; ++j) {
-        if (j < total) {
-            ring_issue(ring, j, g_issue, nm, lc, u, v);
+        if (j < geo.total) {
+            ring_issue(ring, j, g_issue, nm, geo.lc, u, v);
             g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+            pol.issue(j);
         }
         cp_async_commit();
     }
-    for (int m = 0; m < total; m += 3) {
-        temporal_beat<T, K, RX, 0>(m, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
-        temporal_beat<T, K, RX, 1>(m + 1, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
-        temporal_beat<T, K, RX, 2>(m + 2, total, W, ring, g_issue, nn, nm, lc, u, v, un, vn, r0, sc, st_lane, p);
+    for (int m = 0; m < geo.total; m += 3) {
+        pipeline_beat<T, K, 0>(m, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
+        pipeline_beat<T, K, 1>(m + 1, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
+        pipeline_beat<T, K, 2>(m + 2, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
     }
     cp_async_wait<0>();
+}
+
+// Forward policy: Eq. 1 at every stage; the last stage's owned rows are stored.
+template <typename T, int K, int RX>
+struct ForwardPolicy {
+    const Coef<T> &p;
+    const StripGeom &geo;
+    T *__restrict__ un;
+    T *__restrict__ vn;
+    int nm;
+    __device__ __forceinline__ void issue(int) {}
+    __device__ __forceinline__ void begin_beat(int) {}
+    __device__ __forceinline__ void stage(int, const Slice<T> &A, const Slice<T> &B, const Slice<T> &C,
+                                          T wu, T eu, T wv, T ev, int, Slice<T> &out) {
+        slice_update<T, RX>(A, B, C, wu, eu, wv, ev, p, out);
+    }
+    __device__ __forceinline__ void finish(int q, const Slice<T> &out) {
+        const int orow = q - K;
+        if (orow >= 0 && geo.st_lane) {
+            const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
+            store_vec<T>(un + off, out.u);
+            store_vec<T>(vn + off, out.v);
+        }
+    }
+};
+
+// Planes of the K intermediate states written by ForwardAllPolicy.
+template <typename T> struct StagePlanes {
+    T *u[8];
+    T *v[8];
+};
+
+// Forward policy that also stores the owned rows of every stage s (the state
+// s+1 steps ahead) into planes.u[s], planes.v[s]: the states a reverse sweep
+// needs, K per launch.
+template <typename T, int K, int RX>
+struct ForwardAllPolicy {
+    const Coef<T> &p;
+    const StripGeom &geo;
+    const StagePlanes<T> &planes;
+    int nm;
+    __device__ __forceinline__ void issue(int) {}
+    __device__ __forceinline__ void begin_beat(int) {}
+    __device__ __forceinline__ void stage(int s, const Slice<T> &A, const Slice<T> &B, const Slice<T> &C,
+                                          T wu, T eu, T wv, T ev, int q, Slice<T> &out) {
+        slice_update<T, RX>(A, B, C, wu, eu, wv, ev, p, out);
+        const int orow = q - K;
+        if (orow >= 0 && orow < geo.nout && geo.st_lane) {
+            const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
+            store_vec<T>(planes.u[s] + off, out.u);
+            store_vec<T>(planes.v[s] + off, out.v);
+        }
+    }
+    __device__ __forceinline__ void finish(int, const Slice<T> &) {}
+};
+
+// H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
+// needed only narrows the band), which lets a batched launch use one band
+// layout for launches of different depth.
+template <typename T, int K, int H, int RX>
+__device__ __forceinline__ void temporal_strip(int band, int strip, const T *__restrict__ u,
+                                               const T *__restrict__ v, T *__restrict__ un,
+                                               T *__restrict__ vn, int nn, int nm, int rows,
+                                               const Coef<T> &p) {
+    const StripGeom geo = strip_geom<T, K, H>(band, strip, nn, nm, rows);
+    ForwardPolicy<T, K, RX> pol{p, geo, un, vn, nm};
+    pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
 }
 
 }  // namespace rdk
