@@ -291,6 +291,29 @@ def measure_batched(rd, torch, T=5000, quick=False):
             "vs_plain_fwd": ms_p / ms_b}
 
 
+def measure_snapshots(rd, grid, x_dev, torch, T=2000, every=200):
+    """Snapshot capture (the paper's A_show / B_show, every `every` steps to pinned host
+    memory) against the same run without snapshots, on the headline grid."""
+    grid.init(x_dev, 1.0).run(T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grid.init(x_dev, 1.0).run(T)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    grid.init(x_dev, 1.0)
+    us, vs = grid.run_snapshots(T, every, out="host", n_stage=2)  # warm; allocates the pinned outputs
+    grid.init(x_dev, 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grid.run_snapshots(T, every, out="host", n_stage=2, buffers=(us, vs))
+    t_snap = time.perf_counter() - t0
+    n = T // every + 1
+    nbytes = int(2 * n * us[0].numel() * us.element_size())
+    return {"T": T, "every": every, "snapshots": n, "bytes_to_host": nbytes,
+            "ms": t_snap * 1e3, "plain_ms": t_plain * 1e3, "overhead": t_snap / t_plain - 1.0,
+            "host_gbs": nbytes / t_snap / 1e9}
+
+
 def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
     if quick:
         T = 200
@@ -427,6 +450,8 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extras:
+        extra["snapshots"] = measure_snapshots(rd, grid, x_dev, torch, T=200 if args.quick else 2000,
+                                               every=20 if args.quick else 200)
         extra["batched"] = measure_batched(rd, torch, quick=args.quick)
         extra["adjoint"] = measure_adjoint(rd, torch, quick=args.quick)
     cpu = None if args.no_cpu else oracle_sample(6.0 if args.quick else 12.0, n=N)

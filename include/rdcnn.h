@@ -133,6 +133,24 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k);
  * Either output pointer may be NULL to skip that field. */
 int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device);
 
+/* T steps of Eq. 1 with the state captured every `every` steps: the A_show /
+ * B_show arrays of the paper's main loop (Sec. II.B, every test_mod
+ * iterations the state is copied to the host; slot 0 is the initial state).
+ * Snapshot s (s = 0 .. T/every, integer division) is the state after
+ * s * every steps, written to u_snap + s*NN*NM and v_snap + s*NN*NM
+ * (elements of the handle's dtype).  snap_on_device = 1: device arrays,
+ * copied on the bound stream, asynchronous.  snap_on_device = 0: host arrays
+ * (pinned memory lets the copies overlap the steps); each snapshot passes
+ * through a device staging slot of 2 planes taken from `staging`
+ * (staging_bytes / (2 * plane bytes) slots, at least one) and is copied on a
+ * second stream while the run continues; the call returns when every
+ * snapshot has landed.  The final state is left in the bound u, v, as after
+ * rdcnn_run(h, T, AUTO, 0); the results are bit-identical to it.
+ * Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ESPACE (no staging for host
+ * snapshots), RDCNN_ECUDA. */
+int rdcnn_run_snapshots(rdcnn_t *h, int64_t T, int64_t every, void *u_snap, void *v_snap,
+                        int snap_on_device, void *staging, size_t staging_bytes);
+
 /* Release the handle (not the caller's buffers).  NULL is ignored. */
 void rdcnn_destroy(rdcnn_t *h);
 

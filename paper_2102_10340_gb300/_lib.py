@@ -64,6 +64,7 @@ SIGNATURES = [
     ("rdcnn_set_state", c_int, [c_vp, c_vp, c_vp, c_int]),
     ("rdcnn_run", c_int, [c_vp, c_i64, c_int, c_int]),
     ("rdcnn_get_state", c_int, [c_vp, c_vp, c_vp, c_int]),
+    ("rdcnn_run_snapshots", c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_int, c_vp, c_size]),
     ("rdcnn_destroy", None, [c_vp]),
     ("rdcnn_batch_workspace_bytes", c_int, [ctypes.POINTER(Instance), c_int, c_int, ctypes.POINTER(Tune),
                                             ctypes.POINTER(c_size)]),

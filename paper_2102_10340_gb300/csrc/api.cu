@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of include/rdcnn.h for the single-grid calls:
 // handle life cycle, state I/O and the T-step driver (Eq. 1, t = 1..T).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -9,18 +10,6 @@
 
 #include "internal.h"
 #include "rdcnn.h"
-
-struct rdcnn {
-    int64_t nn = 0, nm = 0;
-    rdcnn_params p{};
-    int dtype = RDCNN_F32;
-    int reaction = RDCNN_REACTION_FHN;
-    void *u = nullptr, *v = nullptr, *ws = nullptr;
-    size_t ws_bytes = 0;
-    cudaStream_t stream = nullptr;
-    bool bound = false;
-    int tune_k = 0, tune_rows = 0;
-};
 
 namespace rdk {
 
@@ -40,6 +29,7 @@ int set_error(int code, const char *fmt, ...) {
 }
 
 int cuda_error(cudaError_t e, const char *what) {
+    (void)cudaGetLastError();  // a failed call leaves its code pending; clear it for later launch checks
     return set_error(RDCNN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -173,7 +163,11 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device) {
     return RDCNN_OK;
 }
 
-int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
+}  // extern "C"
+
+namespace rdk {
+
+int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
@@ -201,7 +195,9 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
     void *nu = su, *nv = sv;
     int64_t left = T;
     while (left > 0) {
-        const int kk = (int)(left < k ? left : k);
+        int kk = (int)(left < k ? left : k);
+        const int64_t done = T - left;
+        if (every > 0) kk = (int)std::min<int64_t>(kk, every - done % every);
         cudaError_t e;
         if (variant == RDCNN_VARIANT_TEMPORAL)
             e = launch_temporal(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
@@ -217,6 +213,10 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
         cu = nu; cv = nv;
         nu = const_cast<void *>(tu); nv = const_cast<void *>(tv);
         left -= kk;
+        if (every > 0 && (T - left) % every == 0 && mark) {
+            const int rc = mark(ctx, T - left, cu, cv);
+            if (rc < 0) return rc;
+        }
     }
     if (cu != h->u) {
         cudaError_t e = cudaMemcpyAsync(h->u, cu, plane, cudaMemcpyDeviceToDevice, h->stream);
@@ -225,6 +225,12 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) {
     }
     return RDCNN_OK;
 }
+
+}  // namespace rdk
+
+extern "C" {
+
+int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) { return run_core(h, T, variant, k, 0, nullptr, nullptr); }
 
 int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
@@ -239,6 +245,10 @@ int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device) {
     return RDCNN_OK;
 }
 
-void rdcnn_destroy(rdcnn_t *h) { delete h; }
+void rdcnn_destroy(rdcnn_t *h) {
+    if (!h) return;
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    delete h;
+}
 
 }  // extern "C"

@@ -7,6 +7,20 @@
 
 #include "rdcnn.h"
 
+// The simulation handle behind rdcnn_t (include/rdcnn.h).
+struct rdcnn {
+    int64_t nn = 0, nm = 0;
+    rdcnn_params p{};
+    int dtype = RDCNN_F32;
+    int reaction = RDCNN_REACTION_FHN;
+    void *u = nullptr, *v = nullptr, *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+    int tune_k = 0, tune_rows = 0;
+    cudaStream_t copy_stream = nullptr;  // created on first use by rdcnn_run_snapshots
+};
+
 namespace rdk {
 
 // Launch-shape limits of the vectorised kernels.
@@ -38,6 +52,15 @@ int sm_count();
 // is the one bound by rdcnn_bind (NULL if unbound).
 int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
                 int *reaction, cudaStream_t *stream);
+
+// Callback of run_core: called after the launch that completes step t (a
+// multiple of `every`), with the planes that hold the state at that step.
+typedef int (*MarkFn)(void *ctx, int64_t t, const void *cu, const void *cv);
+
+// Advance the bound state of h by T steps (the body of rdcnn_run).  With
+// every > 0 no launch crosses a multiple of `every`, and mark(ctx, t, ...)
+// runs after each such step t.  Result in h->u, h->v.
+int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx);
 
 // Kernel launchers.  All return the launch status (cudaGetLastError()).
 // u/v are read, un/vn written; the two pairs must not overlap.

@@ -151,6 +151,46 @@ class Grid:
         L.check(self.lib.rdcnn_run(self.h, int(T), _VARIANTS[variant], int(k)))
         return self
 
+    def run_snapshots(self, T: int, every: int, out: str = "host", n_stage: int = 2, pin: bool = True,
+                      buffers=None):
+        """Run T steps and return (u_snaps, v_snaps), each (T // every + 1, NN, NM): snapshot s is the
+        state after s * every steps (the paper's A_show / B_show; s = 0 is the state at the call).
+
+        out = "host": pinned host tensors filled on a second stream while the run continues
+        (staged through n_stage device slots); out = "device": device tensors.  buffers: an
+        optional (u_snaps, v_snaps) pair of the right shape / placement to fill instead.
+        """
+        if int(every) < 1 or int(T) < 0:  # let the library reject it
+            L.check(self.lib.rdcnn_run_snapshots(self.h, int(T), int(every), None, None, 1, None, 0))
+        n = int(T) // int(every) + 1
+        shape = (n, self.nn, self.nm)
+        if buffers is not None:
+            us, vs = buffers
+            for t in (us, vs):
+                if tuple(t.shape) != shape or t.dtype != self.dtype or not t.is_contiguous() \
+                        or t.is_cuda != (out == "device"):
+                    raise ValueError(f"snapshot buffers must be contiguous {shape} {self.dtype} on the {out}")
+        if out == "device":
+            if buffers is None:
+                us = torch.empty(shape, dtype=self.dtype, device=self.device)
+                vs = torch.empty(shape, dtype=self.dtype, device=self.device)
+            staging, sbytes = None, 0
+        elif out == "host":
+            if buffers is None:
+                us = torch.empty(shape, dtype=self.dtype, pin_memory=pin)
+                vs = torch.empty(shape, dtype=self.dtype, pin_memory=pin)
+            staging = torch.empty((int(n_stage), 2, self.nn, self.nm), dtype=self.dtype, device=self.device)
+            sbytes = staging.numel() * staging.element_size()
+        else:
+            raise ValueError("out must be 'host' or 'device'")
+        self._bind()
+        L.check(self.lib.rdcnn_run_snapshots(self.h, int(T), int(every), _vp(us), _vp(vs),
+                                             1 if out == "device" else 0,
+                                             _vp(staging) if staging is not None else None, sbytes))
+        if out == "host":
+            self._last_staging = staging  # copies are complete; kept only until the next call
+        return us, vs
+
     def get_state(self, u_out: torch.Tensor | None = None, v_out: torch.Tensor | None = None):
         """Copy the state into u_out / v_out (host tensors: synchronous; device: async)."""
         for t, name in ((u_out, "u_out"), (v_out, "v_out")):
