@@ -285,10 +285,39 @@ def measure_batched(rd, torch, T=5000, quick=False):
     ms_p = s.elapsed_time(e)
     for g in grids:
         g.close()
+    # on-device search statistics of all instances (reads u and v once: 8 B per cell)
+    b.summary(0.05)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        b.summary(0.05)
+    t_sum = (time.perf_counter() - t0) / 5
     return {"value": cells * T / (ms_b * 1e-3) / 1e9, "unit": "Gcell-updates/s",
             "instances": len(specs), "T": T, "cells": cells, "ms": ms_b, "tune": tune,
             "plain_fwd_value": cells * T / (ms_p * 1e-3) / 1e9, "plain_fwd_ms": ms_p,
-            "vs_plain_fwd": ms_p / ms_b}
+            "vs_plain_fwd": ms_p / ms_b,
+            "summary": {"ms": t_sum * 1e3, "gbs": 8 * cells / t_sum / 1e9,
+                        "note": "rdcnn_batch_summary, all instances, host wall time incl. result copy"}}
+
+
+def measure_search(torch, N=256, T=2000, quick=False):
+    """(Du, Dv) sweep of Sec. III.A: an 8 x 8 grid of genes around the defaults, 16 x 16
+    centre patch, statistics at 4 checkpoints; whole-harness cell-updates/s and labels."""
+    from paper_2102_10340_gb300 import search
+
+    if quick:
+        T = 200
+    genes = search.du_dv_grid(np.linspace(0.05, 0.75, 8), np.linspace(0.3, 1.0, 8))
+    search.sweep(genes[:2], N=N, T=8, checkpoints=1)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = search.sweep(genes, N=N, T=T, checkpoints=4)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    labels = {k: res["labels"].count(k) for k in sorted(set(res["labels"]))}
+    return {"genes": len(genes), "grid": [N, N], "T": T, "ms": dt * 1e3,
+            "value": len(genes) * N * N * T / dt / 1e9, "unit": "Gcell-updates/s (incl. statistics)",
+            "labels": labels}
 
 
 def measure_snapshots(rd, grid, x_dev, torch, T=2000, every=200):
@@ -453,6 +482,7 @@ def run_ours(args):
         extra["snapshots"] = measure_snapshots(rd, grid, x_dev, torch, T=200 if args.quick else 2000,
                                                every=20 if args.quick else 200)
         extra["batched"] = measure_batched(rd, torch, quick=args.quick)
+        extra["search"] = measure_search(torch, quick=args.quick)
         extra["adjoint"] = measure_adjoint(rd, torch, quick=args.quick)
     cpu = None if args.no_cpu else oracle_sample(6.0 if args.quick else 12.0, n=N)
 

@@ -183,6 +183,22 @@ int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int
                     const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
                     void *stream);
 
+/* Statistics of every instance's state, computed on the device for ranking
+ * the instances of a parameter search (Sec. III.A sorts (Du, Dv) into slow
+ * growth, dynamic patterns and dull homogeneous states; Sec. III.B searches
+ * (a, b) for edge-detecting behaviour).  Only nn, nm, u, v of each instance
+ * are used.  out (host, n x 8 doubles), per instance:
+ *   mean(u), var(u), min(u), max(u), mean(v), var(v),
+ *   mean of |u(i+1,j) - u(i,j)| + |u(i,j+1) - u(i,j)| (wrapping), and the
+ *   fraction of cells where that sum exceeds `threshold`.
+ * Variances are population variances.  Work runs on `stream`; the call
+ * returns when `out` is filled.  workspace: device, at least
+ * rdcnn_summary_workspace_bytes.  Errors: RDCNN_EINVAL, RDCNN_ESPACE,
+ * RDCNN_ECUDA. */
+int rdcnn_summary_workspace_bytes(const rdcnn_instance *inst, int n, size_t *bytes);
+int rdcnn_batch_summary(const rdcnn_instance *inst, int n, int dtype, double threshold, double *out,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ adjoint */
 
 /* Bytes of device workspace rdcnn_adjoint needs for T steps with

@@ -17,6 +17,10 @@ Functions and the passages they follow:
 * :func:`adjoint` -- exact discrete adjoint of Eq. 1-3 (not in the paper;
   derivation in ``rdcnn_oracle.c``).
 * :func:`init_state` -- u = v = k_a x (Eq. 1, first line).
+* :func:`summary` -- per-state statistics used to rank the instances of a
+  parameter search (Sec. III.A-III.B): plain definitions (mean, population
+  variance, min, max, wrapped forward-difference gradient sum, fraction of
+  cells above a threshold).
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (fixed point, linearisation, Fourier decay, mass conservation, symmetries,
@@ -165,6 +169,9 @@ class Oracle:
     def run_numpy(self, u, v, params: dict, T: int, reaction: int = FHN):
         return run_numpy(u, v, params, T, reaction)
 
+    def summary(self, u, v, threshold: float, precision=np.float64):
+        return summary(u, v, threshold, precision)
+
 
 def _get() -> Oracle:
     global _default
@@ -224,3 +231,29 @@ def run_numpy(u, v, params: dict, T: int, reaction: int = FHN):
     for _ in range(int(T)):
         u, v = step_numpy(u, v, params, reaction)
     return _plane(u), _plane(v)
+
+
+# ---------------------------------------------------------------------------
+# Statistics of a state for ranking the instances of a parameter search
+# (Sec. III.A sorts (Du, Dv) into slow growth / patterns / dull states).
+# ---------------------------------------------------------------------------
+
+SUMMARY_FIELDS = ("mean_u", "var_u", "min_u", "max_u", "mean_v", "var_v", "grad_u", "edge_frac")
+
+
+def summary(u, v, threshold: float, precision=np.float64) -> np.ndarray:
+    """The 8 statistics of (u, v): mean(u), var(u), min(u), max(u), mean(v), var(v),
+    mean over cells of g = |u(i+1,j) - u(i,j)| + |u(i,j+1) - u(i,j)| (indices wrap), and
+    the fraction of cells with g > threshold.  Sums in FP64; g and the threshold test are
+    evaluated in `precision` (the precision the state was computed in), because that test
+    turns floating point into a count."""
+    u64 = np.asarray(u, dtype=np.float64)
+    v64 = np.asarray(v, dtype=np.float64)
+    up = np.asarray(u, dtype=precision)
+    g = np.abs(np.roll(up, -1, axis=0) - up) + np.abs(np.roll(up, -1, axis=1) - up)
+    n = u64.size
+    mu, mv = u64.sum() / n, v64.sum() / n
+    return np.array([mu, np.sum((u64 - mu) ** 2) / n, u64.min(), u64.max(),
+                     mv, np.sum((v64 - mv) ** 2) / n,
+                     np.asarray(g, dtype=np.float64).sum() / n,
+                     np.count_nonzero(g > np.asarray(threshold, dtype=precision)) / n])

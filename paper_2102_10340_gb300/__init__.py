@@ -23,7 +23,7 @@ def load():
 
 
 def __getattr__(name):
-    if name in ("Grid", "Batch", "RDCNNFunction", "run", "run_static", "launch_count", "DEFAULT_PARAMS", "GRAD_NAMES"):
+    if name in ("Grid", "Batch", "RDCNNFunction", "run", "run_static", "launch_count", "grid_summary", "SUMMARY_FIELDS", "DEFAULT_PARAMS", "GRAD_NAMES"):
         from . import rdcnn
 
         return getattr(rdcnn, name)

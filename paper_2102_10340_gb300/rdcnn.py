@@ -347,6 +347,36 @@ class Batch:
     def state(self, i: int):
         return self.items[i]["u"], self.items[i]["v"]
 
+    def summary(self, threshold: float = 0.05):
+        """Per-instance statistics computed on the device, as a float64 tensor (n, 8):
+        mean(u), var(u), min(u), max(u), mean(v), var(v), mean gradient sum of u,
+        fraction of cells whose gradient sum exceeds `threshold` (see rdcnn_batch_summary)."""
+        return summary(self._table, len(self.items), self.dtype, threshold, self.device)
+
+
+SUMMARY_FIELDS = ("mean_u", "var_u", "min_u", "max_u", "mean_v", "var_v", "grad_u", "edge_frac")
+
+
+def summary(table, n: int, dtype, threshold: float, device):
+    """rdcnn_batch_summary over a ctypes instance table (see Batch.summary)."""
+    lib = L.load()
+    nb = ctypes.c_size_t()
+    L.check(lib.rdcnn_summary_workspace_bytes(table, n, ctypes.byref(nb)))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=device)
+    out = (ctypes.c_double * (8 * n))()
+    L.check(lib.rdcnn_batch_summary(table, n, _dtype_code(dtype), float(threshold), out, _vp(ws), nb.value,
+                                    ctypes.c_void_p(_stream_ptr(device))))
+    return torch.tensor(list(out), dtype=torch.float64).reshape(n, 8)
+
+
+def grid_summary(u: torch.Tensor, v: torch.Tensor, threshold: float = 0.05):
+    """rdcnn_batch_summary of one (u, v) state: a float64 tensor of 8 values (see SUMMARY_FIELDS)."""
+    nn, nm = u.shape
+    _plane_check(v, nn, nm, u.dtype, "v")
+    tab = (L.Instance * 1)()
+    tab[0] = L.Instance(nn, nm, L.params_struct(_params(None)), u.data_ptr(), v.data_ptr(), 0, 0)
+    return summary(tab, 1, u.dtype, threshold, u.device)[0]
+
 
 class RDCNNFunction(torch.autograd.Function):
     """(u0, v0, theta) -> (u_T, v_T), theta = [Du, Dv, a, b, eps, c] (a float64 tensor).

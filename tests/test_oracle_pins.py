@@ -324,3 +324,32 @@ def test_adjoint_zero_steps(oracle_mod):
     x = inp.uniform_field(1, 3, 3)
     lu0, lv0, g = oracle_mod.adjoint(x, x, inp.default_params(), 0, x, 2 * x)
     assert np.array_equal(lu0, x) and np.array_equal(lv0, 2 * x) and np.all(g == 0)
+
+
+# ----------------------------------------------------------------------------- search statistics
+
+def test_summary_uniform_field(oracle_mod):
+    s = oracle_mod.summary(np.full((6, 9), 0.25), np.full((6, 9), -2.0), 0.01)
+    np.testing.assert_array_equal(s, [0.25, 0.0, 0.25, 0.25, -2.0, 0.0, 0.0, 0.0])
+
+
+def test_summary_checkerboard_closed_form(oracle_mod):
+    """+-1 checkerboard of period 2 on an even torus: every cell differs from both forward
+    neighbours by 2, so the gradient sum is 4 everywhere; mean 0, variance 1."""
+    i, j = np.meshgrid(np.arange(8), np.arange(10), indexing="ij")
+    u = np.where((i + j) % 2 == 0, 1.0, -1.0)
+    s = oracle_mod.summary(u, 0.5 * u, 3.9)
+    np.testing.assert_allclose(s, [0.0, 1.0, -1.0, 1.0, 0.0, 0.25, 4.0, 1.0], atol=1e-15)
+    assert oracle_mod.summary(u, u, 4.0)[7] == 0.0  # strict inequality
+
+
+def test_summary_single_bump_wraps(oracle_mod):
+    """One cell of height h at the corner of a 5 x 4 torus: the gradient sum is 2h at the
+    bump and h at the two cells whose forward neighbour (wrapping) is the bump."""
+    h = 0.7
+    u = np.zeros((5, 4))
+    u[0, 0] = h
+    s = oracle_mod.summary(u, u, 0.5)
+    assert abs(s[6] - (2 * h + h + h) / 20) < 1e-15
+    assert s[7] == 3 / 20
+    assert abs(s[1] - (h * h / 20 - (h / 20) ** 2)) < 1e-15
