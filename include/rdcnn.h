@@ -66,7 +66,8 @@ enum { RDCNN_REACTION_FHN = 0,                    /* Eq. 2-3 */
 enum { RDCNN_VARIANT_AUTO = 0,                    /* library's choice (temporal when possible) */
        RDCNN_VARIANT_STEP1 = 1,                   /* one launch per time step, float4/double2 rows */
        RDCNN_VARIANT_TEMPORAL = 2,                /* k time steps fused per launch */
-       RDCNN_VARIANT_GENERIC = 3 };               /* scalar path: any size, any alignment */
+       RDCNN_VARIANT_GENERIC = 3,                 /* scalar path: any size, any alignment */
+       RDCNN_VARIANT_TEMPORAL2 = 4 };             /* temporal, the k stages split over two warps */
 
 /* Launch shape: k = time steps fused per launch of the temporal kernels
  * (1..8 F32, 1..4 F64; 0 = library default), rows = grid rows each warp
@@ -120,7 +121,8 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
 
 /* Apply Eq. 1 T times (t = 1..T, Sec. II.A) to the bound state, in place.
  * variant: RDCNN_VARIANT_*; k: time steps fused per launch for the temporal
- * variant (0 = library default; 1..8 for F32, 1..4 for F64).  T = 0 is a
+ * variants (0 = library default; 1..8 for F32, 1..4 for F64).  All variants
+ * give bit-identical results; they differ only in speed.  T = 0 is a
  * no-op.  Asynchronous on the bound stream.  The vectorised variants need
  * NM to be a multiple of 4 (F32) or 2 (F64) and 16-byte aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns

@@ -35,6 +35,7 @@ VARIANT_AUTO = 0
 VARIANT_STEP1 = 1
 VARIANT_TEMPORAL = 2
 VARIANT_GENERIC = 3
+VARIANT_TEMPORAL2 = 4
 
 PARAM_FIELDS = ("dt", "a", "b", "eps", "c", "Du", "Dv")
 STATIC_SCRATCH_BYTES = 16 << 20  # RDCNN_STATIC_SCRATCH_BYTES

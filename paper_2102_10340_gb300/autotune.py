@@ -11,10 +11,12 @@ import torch
 
 _cache: dict = {}
 
-GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (32, 64, 128, 256)] + \
-                      [("step1", 1, r) for r in (8, 16, 32)]
-GRID_CANDIDATES_F64 = [("temporal", k, r) for k in (2, 3, 4) for r in (32, 64, 128)] + \
-                      [("step1", 1, r) for r in (8, 16, 32)]
+GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (0, 32, 64, 128, 256)] + \
+                      [("temporal2", k, r) for k in (4, 6, 8) for r in (0, 64, 176, 256)] + \
+                      [("step1", 1, r) for r in (4, 8, 16)]
+GRID_CANDIDATES_F64 = [("temporal", k, r) for k in (2, 3, 4) for r in (0, 32, 64, 128)] + \
+                      [("temporal2", k, r) for k in (2, 4) for r in (0, 64)] + \
+                      [("step1", 1, r) for r in (4, 8, 16)]
 BATCH_CANDIDATES = [(k, r) for k in (2, 3, 4, 6, 8) for r in (16, 32, 64, 128)]
 
 

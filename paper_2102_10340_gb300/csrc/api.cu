@@ -171,7 +171,7 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
-    if (variant < RDCNN_VARIANT_AUTO || variant > RDCNN_VARIANT_GENERIC)
+    if (variant < RDCNN_VARIANT_AUTO || variant > RDCNN_VARIANT_TEMPORAL2)
         return set_error(RDCNN_EINVAL, "unknown variant %d", variant);
     if (T == 0) return RDCNN_OK;
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
@@ -180,11 +180,12 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
     const bool vec_ok = (h->nm % vec_width(h->dtype) == 0) && aligned16(h->u) && aligned16(h->v) &&
                         aligned16(su) && aligned16(sv);
     if (variant == RDCNN_VARIANT_AUTO) variant = vec_ok ? RDCNN_VARIANT_TEMPORAL : RDCNN_VARIANT_GENERIC;
-    if ((variant == RDCNN_VARIANT_STEP1 || variant == RDCNN_VARIANT_TEMPORAL) && !vec_ok)
+    if ((variant == RDCNN_VARIANT_STEP1 || variant == RDCNN_VARIANT_TEMPORAL ||
+         variant == RDCNN_VARIANT_TEMPORAL2) && !vec_ok)
         return set_error(RDCNN_EINVAL,
                          "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
                          vec_width(h->dtype));
-    if (variant == RDCNN_VARIANT_TEMPORAL) {
+    if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2) {
         if (k == 0) k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
         if (k < 1 || k > max_k(h->dtype))
             return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(h->dtype));
@@ -199,7 +200,10 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
         const int64_t done = T - left;
         if (every > 0) kk = (int)std::min<int64_t>(kk, every - done % every);
         cudaError_t e;
-        if (variant == RDCNN_VARIANT_TEMPORAL)
+        if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
+            e = launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                                      h->tune_rows, h->stream);  // 0 = chosen by the launcher
+        else if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
             e = launch_temporal(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
                                 h->tune_rows, h->stream);  // 0 = chosen by the launcher
         else if (variant == RDCNN_VARIANT_STEP1)

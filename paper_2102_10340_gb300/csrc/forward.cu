@@ -25,6 +25,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "temporal.cuh"
+#include "temporal_split.cuh"
 
 namespace rdk {
 
@@ -116,6 +117,17 @@ k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
     if (wid >= nwarps) return;  // whole warps only
     constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
     temporal_strip<T, K, H, RX>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
+}
+
+// One warp pair per (band, strip): stages split between the two warps
+// (temporal_split.cuh).  Both warps of a pair see the same `item`.
+template <typename T, int K, int RX>
+__global__ void __launch_bounds__(kSplitBlock)
+k_temporal_split(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
+                 T *__restrict__ vn, int nn, int nm, int bands, int nitems, int rows, Coef<T> p) {
+    const int item = blockIdx.x * kSplitPairs + ((threadIdx.x >> 5) >> 1);
+    if (item >= nitems) return;  // the whole pair, before any barrier
+    temporal_split_item<T, K, RX>(item, bands, u, v, un, vn, nn, nm, rows, p);
 }
 
 // --------------------------------------------------------------------------- generic
@@ -244,6 +256,45 @@ cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, vo
     return cudaGetLastError();
 }
 
+template <typename T, int K, int RX>
+int split_blocks_per_sm() {
+    static int cached = -1;
+    if (cached < 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_temporal_split<T, K, RX>, kSplitBlock, 0) !=
+            cudaSuccess)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+template <typename T, int K>
+cudaError_t split_tk(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
+                     int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
+    constexpr int V = Vec<T>::N;
+    constexpr int H = (K + V - 1) / V;
+    constexpr int OUTW = (32 - 2 * H) * V;
+    const int bands = (int)((nm + OUTW - 1) / OUTW);
+    if (rows <= 0) {
+        const int bps = reaction == RDCNN_REACTION_FHN ? split_blocks_per_sm<T, K, RX_FHN>()
+                                                       : split_blocks_per_sm<T, K, RX_NONE>();
+        rows = auto_rows_temporal(K, nn, nm, bands, bps, kSplitPairs);
+    }
+    const int strips = (int)((nn + rows - 1) / rows);
+    const int64_t nitems = (int64_t)bands * strips;
+    const unsigned grid = (unsigned)((nitems + kSplitPairs - 1) / kSplitPairs);
+    const Coef<T> c = make_coef<T>(p, reaction);
+    if (reaction == RDCNN_REACTION_FHN)
+        k_temporal_split<T, K, RX_FHN><<<grid, kSplitBlock, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nitems, rows, c);
+    else
+        k_temporal_split<T, K, RX_NONE><<<grid, kSplitBlock, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nitems, rows, c);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t generic_t(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
                       int64_t nm, const rdcnn_params &p, cudaStream_t s) {
@@ -299,6 +350,29 @@ cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const
         case 6: return temporal_tk<float, 6>(reaction, u, v, un, vn, nn, nm, p, rows, s);
         case 7: return temporal_tk<float, 7>(reaction, u, v, un, vn, nn, nm, p, rows, s);
         case 8: return temporal_tk<float, 8>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
+                                  void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                                  int rows, cudaStream_t s) {
+    if (dtype == RDCNN_F64) {
+        switch (k) {
+            case 2: return split_tk<double, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 3: return split_tk<double, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 4: return split_tk<double, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (k) {
+        case 2: return split_tk<float, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 3: return split_tk<float, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 4: return split_tk<float, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 5: return split_tk<float, 5>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 6: return split_tk<float, 6>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 7: return split_tk<float, 7>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 8: return split_tk<float, 8>(reaction, u, v, un, vn, nn, nm, p, rows, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -70,6 +70,10 @@ cudaError_t launch_step1(int dtype, int reaction, const void *u, const void *v, 
 cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const void *v,
                             void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                             int rows, cudaStream_t s);
+// The temporal pipeline with the K stages split across a warp pair (k >= 2).
+cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
+                                  void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+                                  int rows, cudaStream_t s);
 cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v, void *un,
                            void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                            cudaStream_t s);

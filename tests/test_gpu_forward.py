@@ -27,6 +27,7 @@ def _variants(nm, dtype):
     if nm % vec == 0:
         out += [("step1", 0), ("temporal", 1), ("temporal", 2)]
         out += [("temporal", k) for k in ((3, 4, 5, 8) if dtype == F32 else (3, 4))]
+        out += [("temporal2", k) for k in ((2, 5, 8) if dtype == F32 else (2, 4))]
     return out
 
 
@@ -72,7 +73,7 @@ def test_ragged_and_tiny_grids(rd, oracle_mod, shape, dtype):
 def test_launch_shape_does_not_change_bits(rd, rows):
     x = f32(inp.uniform_field(9, 70, 136))
     base = gpu_run(rd, x, -x, inp.default_params(), 23, F32, "generic")
-    for variant, k in (("step1", 0), ("temporal", 3), ("temporal", 8)):
+    for variant, k in (("step1", 0), ("temporal", 3), ("temporal", 8), ("temporal2", 3), ("temporal2", 8)):
         got = gpu_run(rd, x, -x, inp.default_params(), 23, F32, variant, k, rows=rows)
         assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1]), (variant, k, rows)
 
@@ -197,7 +198,9 @@ def test_temporal_matches_step1_at_full_size_bitwise(rd):
     x = f32(inp.mid_patch(3, N, N)) + f32(0.05 * inp.uniform_field(4, N, N))
     a = gpu_run(rd, x, x, inp.default_params(), 24, F32, "temporal", 4)
     b = gpu_run(rd, x, x, inp.default_params(), 24, F32, "step1")
+    c = gpu_run(rd, x, x, inp.default_params(), 24, F32, "temporal2", 8)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(c[0], b[0]) and np.array_equal(c[1], b[1])
 
 
 def test_misaligned_views_use_generic_or_fail_loudly(rd, oracle_mod):
