@@ -447,18 +447,21 @@ def run_ours(args):
 
     peaks = load_peaks()
     # roofline of the dominant kernel (one launch advances k steps over the whole grid)
-    k = tune["k"] if variant == "temporal" else 1
+    fused = variant in ("temporal", "temporal2")
+    k = tune["k"] if fused else 1
     launch_ms = measure_launch_ms(rd, grid, variant, k, 2, 20, torch)
     cells = N * N
-    if variant == "temporal" and k > 1:
+    if fused and k > 1:
         flops = FLOPS_PER_CELL_STEP * cells * k
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = flops / (launch_ms * 1e-3) / 1e12
-        traffic, tsrc = profiled_traffic(f"k_temporal_f32_k{k}_4096.md") if N == 4096 else (None, "other grid")
+        kname = "k_temporal" if variant == "temporal" else "k_temporal_split"
+        traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md") if N == 4096
+                         else (None, "other grid"))
         roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
                     "traffic": traffic, "traffic_source": tsrc,
-                    "algorithmic_bytes": BYTES_PER_CELL_STEP * cells, "kernel": f"k_temporal<float,K={k}>",
+                    "algorithmic_bytes": BYTES_PER_CELL_STEP * cells, "kernel": f"{kname}<float,K={k}>",
                     "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz "
                                    f"({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})",
                     "launch_ms": launch_ms,
