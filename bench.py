@@ -117,11 +117,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def profiled_traffic(kernel_md: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged.
+def profiled_traffic(kernel_md: str, k: int, rows: int):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel and its launch shape
+    are unchanged.
 
-    The summary records a hash of the kernel sources it was captured from; a
-    different hash (the kernel changed since) yields None.
+    The summary records a hash of the headers that define the kernel's device code and the
+    (k, rows) it was captured with; a different hash or shape yields None.
     """
     import hashlib
     import re
@@ -133,11 +134,14 @@ def profiled_traffic(kernel_md: str):
         return None, "no profile"
     m = re.search(r"source-sha256-16:\s*([0-9a-f]{16})", text)
     t = re.search(r"dram traffic per launch:\s*([0-9.]+)\s*MB", text)
-    if not m or not t:
-        return None, "profile lacks hash or traffic"
+    shape = re.search(r"launch shape:\s*k=(\d+)\s+rows=(\d+)", text)
+    if not m or not t or not shape:
+        return None, "profile lacks hash, shape or traffic"
+    if (int(shape.group(1)), int(shape.group(2))) != (int(k), int(rows)):
+        return None, f"profile taken at k={shape.group(1)} rows={shape.group(2)}"
     csrc = os.path.join(ROOT, "paper_2102_10340_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("common.cuh", "temporal.cuh", "forward.cu"):
+    for f in ("common.cuh", "temporal.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != m.group(1):
@@ -457,7 +461,7 @@ def run_ours(args):
         peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = flops / (launch_ms * 1e-3) / 1e12
         kname = "k_temporal" if variant == "temporal" else "k_temporal_split"
-        traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md") if N == 4096
+        traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md", k, tune["rows"]) if N == 4096
                          else (None, "other grid"))
         roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
                     "traffic": traffic, "traffic_source": tsrc,
@@ -519,7 +523,9 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
-    ap.add_argument("--variant", default="temporal", choices=("temporal", "step1", "generic"))
+    ap.add_argument("--leg", choices=("batched", "adjoint", "search"), default=None,
+                    help="run only this follow-on measurement (small, for profiling) and print it")
+    ap.add_argument("--variant", default="temporal", choices=("temporal", "temporal2", "step1", "generic"))
     ap.add_argument("--k", type=int, default=8)
     ap.add_argument("--rows", type=int, default=128)
     args = ap.parse_args(argv)
@@ -527,6 +533,16 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        import torch
+
+        from paper_2102_10340_gb300 import rdcnn as rd
+
+        fn = {"batched": lambda: measure_batched(rd, torch, quick=True),
+              "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
+              "search": lambda: measure_search(torch, quick=True)}[args.leg]
+        print(json.dumps({"leg": args.leg, **fn()}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -32,7 +32,6 @@ namespace rdk {
 namespace {
 
 constexpr int kStep1Block = 256;
-constexpr int kTemporalBlock = 32 * kTemporalWarps;
 
 // --------------------------------------------------------------------------- single step
 
@@ -108,16 +107,6 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
 }
 
 // --------------------------------------------------------------------------- temporal blocking
-
-template <typename T, int K, int RX>
-__global__ void __launch_bounds__(kTemporalBlock)
-k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
-           T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
-    const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
-    if (wid >= nwarps) return;  // whole warps only
-    constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
-    temporal_strip<T, K, H, RX>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
-}
 
 // One warp pair per (band, strip): stages split between the two warps
 // (temporal_split.cuh).  Both warps of a pair see the same `item`.

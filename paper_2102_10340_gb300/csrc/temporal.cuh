@@ -239,4 +239,18 @@ __device__ __forceinline__ void temporal_strip(int band, int strip, const T *__r
     pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
 }
 
+constexpr int kTemporalBlock = 32 * kTemporalWarps;
+
+// The single-grid temporally blocked kernel: warp w of the launch owns work
+// item (band w % bands, strip w / bands).
+template <typename T, int K, int RX>
+__global__ void __launch_bounds__(kTemporalBlock)
+k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
+           T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
+    const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
+    if (wid >= nwarps) return;  // whole warps only
+    constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
+    temporal_strip<T, K, H, RX>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
+}
+
 }  // namespace rdk
