@@ -13,6 +13,12 @@ Functions and the passages they follow:
 * :func:`step_numpy`, :func:`run_numpy` -- the same model restated as whole-
   array numpy code with ``np.roll`` for the periodic neighbours (the array
   form of Sec. II.D).  A second formulation used to cross-check the C loops.
+* ``boundary=ZEROFLUX`` -- no flux across the grid edge (the ghost cell
+  beyond an edge holds the edge cell's value); ``reaction=CENN`` -- the
+  Chua-Yang cellular neural network cell (output y = (|x+1| - |x-1|)/2,
+  feedback centre c, arms Du, offset plane w held in v).  Sec. I and II.A
+  present the framework as a template for such models without fixing one;
+  both are readings, written out in ``rdcnn_oracle.c``.
 * :func:`scalar_map` -- Eq. 1 for an isolated cell (no diffusion term).
 * :func:`adjoint` -- exact discrete adjoint of Eq. 1-3 (not in the paper;
   derivation in ``rdcnn_oracle.c``).
@@ -41,6 +47,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FHN = 0
 NONE = 1
+CENN = 2
+
+PERIODIC = 0
+ZEROFLUX = 1
 
 # Sec. II.A: get_init_state() defaults  a=-0.3, b=1.3, eps=-0.1, c=1, Du=0.06, Dv=1, dt=0.1
 PARAM_ORDER = ("dt", "a", "b", "eps", "c", "Du", "Dv")
@@ -91,6 +101,9 @@ class Oracle:
 
     FHN = FHN
     NONE = NONE
+    CENN = CENN
+    PERIODIC = PERIODIC
+    ZEROFLUX = ZEROFLUX
 
     def __init__(self, lib_path: str):
         lib = ctypes.CDLL(lib_path)
@@ -100,6 +113,11 @@ class Oracle:
         lib.oracle_step.restype = None
         lib.oracle_run.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, i64, ctypes.c_int]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_step_bc.argtypes = [i64, i64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int]
+        lib.oracle_step_bc.restype = None
+        lib.oracle_run_bc.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int]
+        lib.oracle_run_bc.restype = ctypes.c_int
         lib.oracle_scalar_map.argtypes = [ctypes.c_double, ctypes.c_double, dp, i64, dp, dp, dp, dp]
         lib.oracle_scalar_map.restype = None
         lib.oracle_adjoint.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, i64, dp, dp, i64,
@@ -115,23 +133,34 @@ class Oracle:
     def max_threads(self) -> int:
         return int(self.lib.oracle_max_threads())
 
-    def step(self, u, v, params: dict, reaction: int = FHN, nthreads: int = 1):
+    def step(self, u, v, params: dict, reaction: int = FHN, nthreads: int = 1,
+             boundary: int = PERIODIC):
         """One Jacobi application of Eq. 1 on the whole grid (C loops, FP64)."""
         u = _plane(u); v = _plane(v)
         nn, nm = u.shape
         un = np.empty_like(u); vn = np.empty_like(v)
         p = pvec(params)
-        self.lib.oracle_step(nn, nm, _ptr(u), _ptr(v), _ptr(un), _ptr(vn), _ptr(p), reaction, nthreads)
+        if boundary == PERIODIC:
+            self.lib.oracle_step(nn, nm, _ptr(u), _ptr(v), _ptr(un), _ptr(vn), _ptr(p), reaction,
+                                 nthreads)
+        else:
+            self.lib.oracle_step_bc(nn, nm, _ptr(u), _ptr(v), _ptr(un), _ptr(vn), _ptr(p), reaction,
+                                    boundary, nthreads)
         return un, vn
 
-    def run(self, u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1):
+    def run(self, u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1,
+            boundary: int = PERIODIC):
         """T applications of Eq. 1 (t = 1..T); returns new arrays (u_T, v_T)."""
         u = _plane(u).copy(); v = _plane(v).copy()
         if u.ndim != 2 or u.shape != v.shape:
             raise ValueError("u and v must be 2-D planes of the same shape")
         nn, nm = u.shape
         p = pvec(params)
-        rc = self.lib.oracle_run(nn, nm, _ptr(u), _ptr(v), _ptr(p), reaction, int(T), nthreads)
+        if boundary == PERIODIC:
+            rc = self.lib.oracle_run(nn, nm, _ptr(u), _ptr(v), _ptr(p), reaction, int(T), nthreads)
+        else:
+            rc = self.lib.oracle_run_bc(nn, nm, _ptr(u), _ptr(v), _ptr(p), reaction, boundary, int(T),
+                                        nthreads)
         if rc != 0:
             raise RuntimeError("oracle_run failed")
         return u, v
@@ -163,11 +192,11 @@ class Oracle:
             raise RuntimeError("oracle_adjoint failed")
         return lu0, lv0, g
 
-    def step_numpy(self, u, v, params: dict, reaction: int = FHN):
-        return step_numpy(u, v, params, reaction)
+    def step_numpy(self, u, v, params: dict, reaction: int = FHN, boundary: int = PERIODIC):
+        return step_numpy(u, v, params, reaction, boundary)
 
-    def run_numpy(self, u, v, params: dict, T: int, reaction: int = FHN):
-        return run_numpy(u, v, params, T, reaction)
+    def run_numpy(self, u, v, params: dict, T: int, reaction: int = FHN, boundary: int = PERIODIC):
+        return run_numpy(u, v, params, T, reaction, boundary)
 
     def summary(self, u, v, threshold: float, precision=np.float64):
         return summary(u, v, threshold, precision)
@@ -186,12 +215,13 @@ def max_threads() -> int:
     return _get().max_threads()
 
 
-def step(u, v, params: dict, reaction: int = FHN, nthreads: int = 1):
-    return _get().step(u, v, params, reaction, nthreads)
+def step(u, v, params: dict, reaction: int = FHN, nthreads: int = 1, boundary: int = PERIODIC):
+    return _get().step(u, v, params, reaction, nthreads, boundary)
 
 
-def run(u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1):
-    return _get().run(u, v, params, T, reaction, nthreads)
+def run(u, v, params: dict, T: int, reaction: int = FHN, nthreads: int = 1,
+        boundary: int = PERIODIC):
+    return _get().run(u, v, params, T, reaction, nthreads, boundary)
 
 
 def scalar_map(u0: float, v0: float, params: dict, T: int):
@@ -208,28 +238,38 @@ def adjoint(u0, v0, params: dict, T: int, lu_T, lv_T, n_checkpoints: int = 0,
 # Written independently of the C loops above; used only as a cross-check.
 # ---------------------------------------------------------------------------
 
-def _lap_roll(f: np.ndarray) -> np.ndarray:
-    north = np.roll(f, 1, axis=0)    # value at row i-1
-    south = np.roll(f, -1, axis=0)   # value at row i+1
-    west = np.roll(f, 1, axis=1)     # value at column j-1
-    east = np.roll(f, -1, axis=1)    # value at column j+1
+def _neighbours(f: np.ndarray, boundary: int = PERIODIC):
+    """(north, south, west, east) neighbour planes: values at rows i-1 / i+1 and
+    columns j-1 / j+1.  Periodic: np.roll; zero flux: edge-replicated padding."""
+    if boundary == PERIODIC:
+        return np.roll(f, 1, axis=0), np.roll(f, -1, axis=0), np.roll(f, 1, axis=1), np.roll(f, -1, axis=1)
+    g = np.pad(f, 1, mode="edge")
+    return g[:-2, 1:-1], g[2:, 1:-1], g[1:-1, :-2], g[1:-1, 2:]
+
+
+def _lap_roll(f: np.ndarray, boundary: int = PERIODIC) -> np.ndarray:
+    north, south, west, east = _neighbours(f, boundary)
     return north + south + west + east - 4.0 * f
 
 
-def step_numpy(u, v, params: dict, reaction: int = FHN):
+def step_numpy(u, v, params: dict, reaction: int = FHN, boundary: int = PERIODIC):
     u = _plane(u); v = _plane(v)
     dt, a, b, eps, c, Du, Dv = pvec(params)
+    if reaction == CENN:
+        y = np.clip(u, -1.0, 1.0)                 # the saturating output, as a clamp
+        return u + dt * (-u + c * y + Du * sum(_neighbours(y, boundary)) + v), v.copy()
     if reaction == FHN:
         f1 = c * u - u ** 3 / 3.0 - v
         f2 = -eps * (u - b * v + a)
     else:
         f1 = np.zeros_like(u); f2 = np.zeros_like(v)
-    return u + dt * (f1 + Du * _lap_roll(u)), v + dt * (f2 + Dv * _lap_roll(v))
+    return (u + dt * (f1 + Du * _lap_roll(u, boundary)),
+            v + dt * (f2 + Dv * _lap_roll(v, boundary)))
 
 
-def run_numpy(u, v, params: dict, T: int, reaction: int = FHN):
+def run_numpy(u, v, params: dict, T: int, reaction: int = FHN, boundary: int = PERIODIC):
     for _ in range(int(T)):
-        u, v = step_numpy(u, v, params, reaction)
+        u, v = step_numpy(u, v, params, reaction, boundary)
     return _plane(u), _plane(v)
 
 

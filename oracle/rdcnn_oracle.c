@@ -28,6 +28,21 @@
  * Parameter vector p[7] = {dt, a, b, eps, c, Du, Dv} (the order the paper's
  * "Pars" vector is indexed in, Sec. II.B).
  *
+ * Model variants (Sec. I and Sec. II.A say the framework is a template for
+ * other cellular nonlinear / FDTD models, naming the Chua-Yang cellular
+ * neural network; no second model is specified, so these are readings):
+ *  - boundary ZEROFLUX: no flux across the grid edge, i.e. the ghost cell
+ *    beyond an edge holds the value of the edge cell itself (the neighbour
+ *    index is clamped into the grid instead of wrapped);
+ *  - reaction CENN: the Chua-Yang cell with the piecewise-linear output
+ *    y(x) = (|x + 1| - |x - 1|) / 2, a cross-shaped feedback template
+ *    (centre c, the four arms Du, corners 0) and a constant offset plane w
+ *    carried in v (the control template's response to the input image plus
+ *    the bias):
+ *      x_ij <- x_ij + dt [ -x_ij + c y(x_ij) + Du (y_N + y_S + y_W + y_E) + w_ij ],
+ *      w_ij <- w_ij.
+ *    a, b, eps and Dv are unused.
+ *
  * The adjoint (oracle_adjoint) is not in the paper.  It is the exact discrete
  * adjoint (reverse-mode derivative) of the map above, derived by
  * differentiating Eq. 1-3 with respect to u_ij, v_ij and the gene; the
@@ -50,13 +65,30 @@
 #define P_DV 6
 
 /* reaction selector: 0 = FitzHugh-Nagumo (Eq. 2-3); 1 = none (f1 = f2 = 0,
- * pure diffusion, used only to pin the stencil against closed forms). */
+ * pure diffusion, used only to pin the stencil against closed forms);
+ * 2 = Chua-Yang cellular neural network cell (see the header). */
 #define ORACLE_FHN 0
 #define ORACLE_NONE 1
+#define ORACLE_CENN 2
+
+/* boundary selector: 0 = toroidal wrap; 1 = zero flux (ghost = edge cell) */
+#define ORACLE_PERIODIC 0
+#define ORACLE_ZEROFLUX 1
 
 static int64_t wrap_index(int64_t i, int64_t n) {
     int64_t r = i % n;
     return r < 0 ? r + n : r;
+}
+
+/* Index of the cell that stands in for neighbour index i (i may be -1 or n). */
+static int64_t neighbour_index(int64_t i, int64_t n, int boundary) {
+    if (boundary == ORACLE_ZEROFLUX) return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+    return wrap_index(i, n);
+}
+
+/* Chua-Yang output function: linear on [-1, 1], saturated outside. */
+static double cenn_output(double x) {
+    return 0.5 * (fabs(x + 1.0) - fabs(x - 1.0));
 }
 
 /* Eq. 2 */
@@ -69,13 +101,30 @@ static double reaction_f2(double u, double v, const double *p) {
     return -p[P_EPS] * (u - p[P_B] * v + p[P_A]);
 }
 
-/* Discrete 5-point Laplacian of plane f at (i, j) with toroidal wrap (Eq. 1). */
-static double laplacian(const double *f, int64_t nn, int64_t nm, int64_t i, int64_t j) {
-    int64_t ip = wrap_index(i + 1, nn), im = wrap_index(i - 1, nn);
-    int64_t jp = wrap_index(j + 1, nm), jm = wrap_index(j - 1, nm);
+/* Discrete 5-point Laplacian of plane f at (i, j) (Eq. 1); the neighbours
+ * beyond the edge follow the boundary selector. */
+static double laplacian_bc(const double *f, int64_t nn, int64_t nm, int64_t i, int64_t j,
+                           int boundary) {
+    int64_t ip = neighbour_index(i + 1, nn, boundary), im = neighbour_index(i - 1, nn, boundary);
+    int64_t jp = neighbour_index(j + 1, nm, boundary), jm = neighbour_index(j - 1, nm, boundary);
     double vert = f[ip * nm + j] + f[im * nm + j];
     double horz = f[i * nm + jm] + f[i * nm + jp];
     return (vert + horz) - 4.0 * f[i * nm + j];
+}
+
+/* The toroidal Laplacian of the paper's model. */
+static double laplacian(const double *f, int64_t nn, int64_t nm, int64_t i, int64_t j) {
+    return laplacian_bc(f, nn, nm, i, j, ORACLE_PERIODIC);
+}
+
+/* Sum of the CeNN outputs y of the four neighbours of (i, j). */
+static double neighbour_output_sum(const double *x, int64_t nn, int64_t nm, int64_t i, int64_t j,
+                                   int boundary) {
+    int64_t ip = neighbour_index(i + 1, nn, boundary), im = neighbour_index(i - 1, nn, boundary);
+    int64_t jp = neighbour_index(j + 1, nm, boundary), jm = neighbour_index(j - 1, nm, boundary);
+    double vert = cenn_output(x[im * nm + j]) + cenn_output(x[ip * nm + j]);
+    double horz = cenn_output(x[i * nm + jm]) + cenn_output(x[i * nm + jp]);
+    return vert + horz;
 }
 
 static void set_threads(int nthreads) {
@@ -95,12 +144,14 @@ int oracle_max_threads(void) {
 }
 
 /*
- * One application of Eq. 1 to the whole grid: (u, v) -> (un, vn).
- * The four buffers must be distinct.  Rows are independent, so the row loop
- * may be split across threads without changing any result.
+ * One application of the update to the whole grid: (u, v) -> (un, vn), with
+ * the given reaction and boundary.  The four buffers must be distinct.  Rows
+ * are independent, so the row loop may be split across threads without
+ * changing any result.
  */
-void oracle_step(int64_t nn, int64_t nm, const double *u, const double *v,
-                 double *un, double *vn, const double *p, int reaction, int nthreads) {
+void oracle_step_bc(int64_t nn, int64_t nm, const double *u, const double *v,
+                    double *un, double *vn, const double *p, int reaction, int boundary,
+                    int nthreads) {
     set_threads(nthreads);
     const double dt = p[P_DT], Du = p[P_DU], Dv = p[P_DV];
 #pragma omp parallel for schedule(static) if (nthreads != 1)
@@ -108,8 +159,16 @@ void oracle_step(int64_t nn, int64_t nm, const double *u, const double *v,
         for (int64_t j = 0; j < nm; ++j) {
             const int64_t c = i * nm + j;
             const double uc = u[c], vc = v[c];
-            const double lu = laplacian(u, nn, nm, i, j);
-            const double lv = laplacian(v, nn, nm, i, j);
+            if (reaction == ORACLE_CENN) {
+                /* state x = u, offset w = v (constant) */
+                const double feedback = p[P_C] * cenn_output(uc)
+                                        + Du * neighbour_output_sum(u, nn, nm, i, j, boundary);
+                un[c] = uc + dt * ((-uc + feedback) + vc);
+                vn[c] = vc;
+                continue;
+            }
+            const double lu = laplacian_bc(u, nn, nm, i, j, boundary);
+            const double lv = laplacian_bc(v, nn, nm, i, j, boundary);
             double r1 = 0.0, r2 = 0.0;
             if (reaction == ORACLE_FHN) {
                 r1 = reaction_f1(uc, vc, p);
@@ -121,12 +180,18 @@ void oracle_step(int64_t nn, int64_t nm, const double *u, const double *v,
     }
 }
 
+/* One application of Eq. 1 on the torus (the paper's model). */
+void oracle_step(int64_t nn, int64_t nm, const double *u, const double *v,
+                 double *un, double *vn, const double *p, int reaction, int nthreads) {
+    oracle_step_bc(nn, nm, u, v, un, vn, p, reaction, ORACLE_PERIODIC, nthreads);
+}
+
 /*
- * T applications of Eq. 1 (t = 1..T), in place on (u, v).  Allocates two
- * scratch planes; returns 0, or -1 when allocation fails or sizes are bad.
+ * T applications of the update (t = 1..T), in place on (u, v).  Allocates
+ * two scratch planes; returns 0, or -1 when allocation fails or sizes are bad.
  */
-int oracle_run(int64_t nn, int64_t nm, double *u, double *v, const double *p,
-               int reaction, int64_t T, int nthreads) {
+int oracle_run_bc(int64_t nn, int64_t nm, double *u, double *v, const double *p,
+                  int reaction, int boundary, int64_t T, int nthreads) {
     if (nn <= 0 || nm <= 0 || T < 0) return -1;
     const size_t n = (size_t)nn * (size_t)nm;
     double *un = (double *)malloc(n * sizeof(double));
@@ -134,7 +199,7 @@ int oracle_run(int64_t nn, int64_t nm, double *u, double *v, const double *p,
     if (!un || !vn) { free(un); free(vn); return -1; }
     double *a = u, *b = v, *an = un, *bn = vn;
     for (int64_t t = 0; t < T; ++t) {
-        oracle_step(nn, nm, a, b, an, bn, p, reaction, nthreads);
+        oracle_step_bc(nn, nm, a, b, an, bn, p, reaction, boundary, nthreads);
         double *ta = a, *tb = b;
         a = an; b = bn; an = ta; bn = tb;
     }
@@ -144,6 +209,12 @@ int oracle_run(int64_t nn, int64_t nm, double *u, double *v, const double *p,
     }
     free(un); free(vn);
     return 0;
+}
+
+/* T applications of Eq. 1 on the torus, in place. */
+int oracle_run(int64_t nn, int64_t nm, double *u, double *v, const double *p,
+               int reaction, int64_t T, int nthreads) {
+    return oracle_run_bc(nn, nm, u, v, p, reaction, ORACLE_PERIODIC, T, nthreads);
 }
 
 /*
@@ -190,13 +261,15 @@ void oracle_scalar_map(double u0, double v0, const double *p, int64_t T,
  * grad[6] = dL/d{Du, Dv, a, b, eps, c}.
  * Forward states are rebuilt from checkpoints taken every S steps
  * (S = ceil(T / n_checkpoints), n_checkpoints <= 0 meaning ceil(sqrt(T))).
- * Returns 0, or -1 on bad sizes or allocation failure.
+ * Returns 0, or -1 on bad sizes, a reaction other than FHN / NONE, or
+ * allocation failure.  The boundary is always toroidal.
  */
 int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
                    const double *p, int reaction, int64_t T,
                    const double *lu_T, const double *lv_T, int64_t n_checkpoints,
                    double *lu0_out, double *lv0_out, double *grad, int nthreads) {
     if (nn <= 0 || nm <= 0 || T < 0) return -1;
+    if (reaction != ORACLE_FHN && reaction != ORACLE_NONE) return -1;
     const size_t n = (size_t)nn * (size_t)nm;
     for (int g = 0; g < 6; ++g) grad[g] = 0.0;
     memcpy(lu0_out, lu_T, n * sizeof(double));

@@ -23,8 +23,8 @@ MUTANTS = {
     "f2_minus_a": ("p[P_B] * v + p[P_A]", "p[P_B] * v - p[P_A]"),
     "f2_sign": ("return -p[P_EPS] * (u", "return p[P_EPS] * (u"),
     "lap_centre_3": ("- 4.0 * f[i * nm + j]", "- 3.0 * f[i * nm + j]"),
-    "lap_north_twice": ("im = wrap_index(i - 1, nn)", "im = wrap_index(i + 1, nn)"),
-    "lap_no_col_wrap": ("jp = wrap_index(j + 1, nm)", "jp = (j + 1 < nm ? j + 1 : j)"),
+    "lap_north_twice": ("im = neighbour_index(i - 1, nn, boundary)", "im = neighbour_index(i + 1, nn, boundary)"),
+    "lap_no_col_wrap": ("jp = neighbour_index(j + 1, nm, boundary)", "jp = (j + 1 < nm ? j + 1 : j)"),
     "du_dv_swapped": ("uc + dt * (r1 + Du * lu)", "uc + dt * (r1 + Dv * lu)"),
     "gauss_seidel": ("r2 = reaction_f2(uc, vc, p);", "r2 = reaction_f2(uc + dt * r1, vc, p);"),
     "dt_squared": ("vn[c] = vc + dt * (r2", "vn[c] = vc + dt * dt * (r2"),
@@ -33,6 +33,14 @@ MUTANTS = {
     "adj_grad_b": ("g[3] += lvk * (eps * vk);", "g[3] += lvk * vk;"),
     "adj_grad_du_uses_v": ("g[0] += luk * laplacian(u,", "g[0] += luk * laplacian(v,"),
     "adj_dv_term": ("rv + Dv * laplacian(lv", "rv + Du * laplacian(lv"),
+    "zf_ghost_past_edge": ("return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);", "return i < 0 ? 1 : (i > n - 1 ? n - 2 : i);"),
+    "zf_ignored": ("if (boundary == ORACLE_ZEROFLUX) return i < 0", "if (0) return i < 0"),
+    "zf_columns_wrap": ("jm = neighbour_index(j - 1, nm, boundary);\n    double vert = f", "jm = wrap_index(j - 1, nm);\n    double vert = f"),
+    "cenn_output_halved": ("0.5 * (fabs(x + 1.0) - fabs(x - 1.0))", "0.25 * (fabs(x + 1.0) - fabs(x - 1.0))"),
+    "cenn_arms_use_state": ("cenn_output(x[im * nm + j]) + cenn_output(x[ip * nm + j])", "x[im * nm + j] + x[ip * nm + j]"),
+    "cenn_no_offset": ("((-uc + feedback) + vc)", "(-uc + feedback)"),
+    "cenn_leak_sign": ("((-uc + feedback) + vc)", "((uc + feedback) + vc)"),
+    "cenn_arm_missing": ("cenn_output(x[i * nm + jm]) + cenn_output(x[i * nm + jp])", "cenn_output(x[i * nm + jp])"),
 }
 
 

@@ -353,3 +353,131 @@ def test_summary_single_bump_wraps(oracle_mod):
     assert abs(s[6] - (2 * h + h + h) / 20) < 1e-15
     assert s[7] == 3 / 20
     assert abs(s[1] - (h * h / 20 - (h / 20) ** 2)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Zero-flux boundary and the CeNN cell (the framework-as-template variants of
+# Sec. I / Sec. II.A; the readings are stated in rdcnn_oracle.c).
+# ---------------------------------------------------------------------------
+
+# Chua-Yang cell gene: feedback centre c, arms Du; a, b, eps, Dv unused.
+CENN_GENE = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 0.2, "Du": 0.05, "Dv": 0.0}
+
+
+def _mirror_extend(f):
+    """Even extension of an N x M plane to a 2N x 2M torus (reflection about the cell faces)."""
+    top = np.concatenate([f, f[:, ::-1]], axis=1)
+    return np.concatenate([top, top[::-1, :]], axis=0)
+
+
+@pytest.mark.parametrize("reaction", ["FHN", "NONE", "CENN"])
+def test_zero_flux_is_the_mirrored_torus_bitwise(oracle_mod, reaction):
+    """A zero-flux N x M grid evolves exactly as the first quadrant of the 2N x 2M torus holding
+    the mirror image: the face between the edge cell and its ghost is a mirror plane, and the
+    periodic model (pinned above) keeps a mirror-symmetric state mirror-symmetric, so the edge
+    cell's outside neighbour is the edge cell itself in both.  Sums are formed in the same order,
+    so equality is bitwise."""
+    rx = getattr(oracle_mod, reaction)
+    gene = CENN_GENE if reaction == "CENN" else ODD_GENE
+    x = 1.6 * inp.uniform_field(21, 7, 10)
+    w = 0.3 * inp.uniform_field(22, 7, 10)
+    ut, vt = oracle_mod.run(x, w, gene, 15, reaction=rx, boundary=oracle_mod.ZEROFLUX)
+    ue, ve = oracle_mod.run(_mirror_extend(x), _mirror_extend(w), gene, 15, reaction=rx)
+    assert np.array_equal(ut, ue[:7, :10]) and np.array_equal(vt, ve[:7, :10])
+    # and the zero-flux answer is not the small torus's
+    up, _ = oracle_mod.run(x, w, gene, 15, reaction=rx)
+    assert not np.allclose(up, ut)
+
+
+@pytest.mark.parametrize("shape,k,l", [((12, 20), 1, 3), ((9, 7), 4, 2), ((16, 5), 0, 1)])
+def test_zero_flux_cosine_mode_decay(oracle_mod, shape, k, l):
+    """Pure diffusion with zero flux: cos(pi k (i + 1/2) / N) cos(pi l (j + 1/2) / M) is an
+    eigenvector of the Neumann 5-point Laplacian with eigenvalue
+    2 cos(pi k / N) - 2 + 2 cos(pi l / M) - 2."""
+    nn, nm = shape
+    i, j = np.meshgrid(np.arange(nn), np.arange(nm), indexing="ij")
+    mode = np.cos(np.pi * k * (i + 0.5) / nn) * np.cos(np.pi * l * (j + 0.5) / nm)
+    par = dict(ODD_GENE)
+    T = 30
+    ut, vt = oracle_mod.run(mode, 0.5 * mode, par, T, reaction=oracle_mod.NONE,
+                            boundary=oracle_mod.ZEROFLUX)
+    lam = 2 * np.cos(np.pi * k / nn) - 2 + 2 * np.cos(np.pi * l / nm) - 2
+    np.testing.assert_allclose(ut, (1 + par["dt"] * par["Du"] * lam) ** T * mode, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(vt, (1 + par["dt"] * par["Dv"] * lam) ** T * 0.5 * mode, rtol=0, atol=1e-12)
+
+
+def test_zero_flux_conserves_mass_without_reaction(oracle_mod):
+    x = inp.uniform_field(5, 11, 14)
+    ut, vt = oracle_mod.run(x, -x, ODD_GENE, 40, reaction=oracle_mod.NONE, boundary=oracle_mod.ZEROFLUX)
+    assert abs(ut.sum() - x.sum()) < 1e-11 and abs(vt.sum() + x.sum()) < 1e-11
+
+
+def test_zero_flux_uniform_field_follows_cell_map(oracle_mod):
+    gene = inp.default_params()
+    ut, vt = oracle_mod.run(np.full((5, 8), 0.37), np.full((5, 8), -0.21), gene, 200,
+                            boundary=oracle_mod.ZEROFLUX)
+    su, sv = oracle_mod.scalar_map(0.37, -0.21, gene, 200)
+    assert np.all(ut == su[-1]) and np.all(vt == sv[-1])
+
+
+@pytest.mark.parametrize("boundary", ["PERIODIC", "ZEROFLUX"])
+def test_cenn_uniform_linear_region_closed_form(oracle_mod, boundary):
+    """|x| < 1 throughout: y(x) = x, so a uniform state obeys x+ = x + dt (-x + (c + 4 Du) x + w):
+    x_T = x* + (x0 - x*) r^T with r = 1 - dt (1 - c - 4 Du), x* = w / (1 - c - 4 Du)."""
+    g = CENN_GENE
+    x0, w = 0.3, 0.2
+    T = 60
+    ut, vt = oracle_mod.run(np.full((6, 5), x0), np.full((6, 5), w), g, T, reaction=oracle_mod.CENN,
+                            boundary=getattr(oracle_mod, boundary))
+    k = 1 - g["c"] - 4 * g["Du"]
+    xs = w / k
+    np.testing.assert_allclose(ut, xs + (x0 - xs) * (1 - g["dt"] * k) ** T, rtol=0, atol=1e-14)
+    assert np.all(vt == w)
+
+
+@pytest.mark.parametrize("x0,expect_star", [(3.0, 3.5), (-3.0, -2.5)])
+def test_cenn_uniform_saturated_closed_form(oracle_mod, x0, expect_star):
+    """|x| > 1 throughout: every output is sign(x), so x+ = x + dt (-x + (c + 4 Du) sign(x) + w)
+    with fixed point x* = (c + 4 Du) sign(x) + w; here c = 2, Du = 0.25, w = 0.5."""
+    g = dict(CENN_GENE, c=2.0, Du=0.25)
+    T = 50
+    ut, _ = oracle_mod.run(np.full((4, 7), x0), np.full((4, 7), 0.5), g, T, reaction=oracle_mod.CENN)
+    np.testing.assert_allclose(ut, expect_star + (x0 - expect_star) * (1 - g["dt"]) ** T, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape,p,q", [((12, 20), 1, 3), ((9, 7), 4, 1)])
+def test_cenn_fourier_mode_linear_region(oracle_mod, shape, p, q):
+    """About the uniform fixed point xbar (|x| < 1), a periodic mode of amplitude d evolves as
+    d_T = d mu^T, mu = 1 + dt (-1 + c + 2 Du (cos(2 pi p / N) + cos(2 pi q / M)))."""
+    nn, nm = shape
+    g = CENN_GENE
+    xbar = 0.2
+    w = xbar * (1 - g["c"] - 4 * g["Du"])
+    mode = inp.fourier_mode(nn, nm, p, q)
+    T = 40
+    ut, _ = oracle_mod.run(xbar + 0.1 * mode, np.full(shape, w), g, T, reaction=oracle_mod.CENN)
+    mu = 1 + g["dt"] * (-1 + g["c"] + 2 * g["Du"] * (np.cos(2 * np.pi * p / nn) + np.cos(2 * np.pi * q / nm)))
+    np.testing.assert_allclose(ut, xbar + 0.1 * mu ** T * mode, rtol=0, atol=1e-13)
+
+
+def test_cenn_uncoupled_bistable_cells_saturate_to_their_sign(oracle_mod):
+    """Du = 0, w = 0, c = 2: each cell is x+ = x + dt (-x + 2 y(x)), whose stable fixed points
+    are +-2 (outputs +-1); a cell starting at x0 != 0 ends at 2 sign(x0)."""
+    g = dict(CENN_GENE, c=2.0, Du=0.0)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.1, 1.5, (6, 9)) * rng.choice([-1.0, 1.0], (6, 9))
+    ut, _ = oracle_mod.run(x, np.zeros_like(x), g, 400, reaction=oracle_mod.CENN,
+                           boundary=oracle_mod.ZEROFLUX)
+    np.testing.assert_allclose(ut, 2.0 * np.sign(x), rtol=0, atol=1e-12)
+
+
+def test_cenn_numpy_formulation_agrees(oracle_mod):
+    """The C loops (|x+1| - |x-1| form) against the numpy clamp form, both boundaries."""
+    x = 2.0 * inp.uniform_field(31, 9, 12)
+    w = 0.4 * inp.uniform_field(32, 9, 12)
+    g = dict(CENN_GENE, c=1.7, Du=0.4)
+    for b in (oracle_mod.PERIODIC, oracle_mod.ZEROFLUX):
+        a = oracle_mod.run(x, w, g, 25, reaction=oracle_mod.CENN, boundary=b)
+        n = oracle_mod.run_numpy(x, w, g, 25, reaction=oracle_mod.CENN, boundary=b)
+        np.testing.assert_allclose(a[0], n[0], rtol=0, atol=1e-12)
+        assert np.array_equal(a[1], w)
