@@ -253,6 +253,34 @@ def measure_launch_ms(rd, grid, variant, k, launches_per_call, reps, torch):
     return float(np.mean([s.elapsed_time(e) for s, e in ev])) / launches_per_call
 
 
+CENN_GENE = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.2, "Du": 0.1, "Dv": 0.0}
+
+
+def measure_models(rd, torch, N=N_GRID, quick=False):
+    """Throughput of the model variants (zero-flux boundary, Chua-Yang CeNN cell) on an N x N
+    FP32 grid: the temporal kernel (k = 8, 128 rows) and the single-step kernel, per launch,
+    CUDA events on the launching stream."""
+    if quick:
+        N = 1024
+    x = torch.from_numpy(np.asarray(inp.uniform_field(7, N, N), dtype=np.float32)).cuda()
+    out = {}
+    for name, reaction, boundary, gene in (("fhn_periodic", "fhn", "periodic", inp.default_params()),
+                                           ("fhn_zeroflux", "fhn", "zeroflux", inp.default_params()),
+                                           ("cenn_periodic", "cenn", "periodic", CENN_GENE),
+                                           ("cenn_zeroflux", "cenn", "zeroflux", CENN_GENE)):
+        g = rd.Grid(N, N, gene, dtype=torch.float32, reaction=reaction, boundary=boundary)
+        g.set_state((1.5 * x).contiguous(), (0.3 * x).contiguous())
+        res = {}
+        for variant, k, rows in (("temporal", 8, 128), ("step1", 1, 0)):
+            g.set_tune(k=k, rows=rows)
+            ms = measure_launch_ms(rd, g, variant, k, 4, 10, torch)
+            res[variant] = {"k": k, "rows": rows, "launch_ms": ms, "gcell_s": N * N * k / (ms * 1e-3) / 1e9}
+        out[name] = res
+        g.close()
+    return {"grid": [N, N], "dtype": "f32", "models": out,
+            "note": "per-launch CUDA-event time; fhn_periodic is the paper's model for comparison"}
+
+
 def measure_batched(rd, torch, T=5000, quick=False):
     specs = inp.sweep_instances(0)
     if quick:
@@ -401,6 +429,7 @@ def run_ours(args):
         tune = autotune.tune_grid(grid, x_dev, trial_steps=max(8, T // 2000))
     grid.set_tune(k=tune["k"], rows=tune["rows"])
     variant = tune["variant"]
+    plan = grid.plan(variant, tune["k"])  # rows = 0 resolves to the launcher's own choice
 
     def barrier():
         if world > 1:
@@ -461,7 +490,7 @@ def run_ours(args):
         peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = flops / (launch_ms * 1e-3) / 1e12
         kname = "k_temporal" if variant == "temporal" else "k_temporal_split"
-        traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md", k, tune["rows"]) if N == 4096
+        traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md", k, plan["rows"]) if N == 4096
                          else (None, "other grid"))
         roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
                     "traffic": traffic, "traffic_source": tsrc,
@@ -491,6 +520,7 @@ def run_ours(args):
         extra["batched"] = measure_batched(rd, torch, quick=args.quick)
         extra["search"] = measure_search(torch, quick=args.quick)
         extra["adjoint"] = measure_adjoint(rd, torch, quick=args.quick)
+        extra["models"] = measure_models(rd, torch, quick=args.quick)
     cpu = None if args.no_cpu else oracle_sample(6.0 if args.quick else 12.0, n=N)
 
     line = {"metric": METRIC, "value": value, "unit": "Gcell-updates/s", "n_gpus": world,
@@ -498,7 +528,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / (PAPER_MCELLS_4096 / 1000.0), "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if (N, T) == (N_GRID, T_STEPS) else f"{N}x{N} FP32 patch, T={T}",
-                       "grid": [N, N], "T": T, "variant": variant, "k": k, "rows": tune["rows"],
+                       "grid": [N, N], "T": T, "variant": variant, "k": k, "rows": plan["rows"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: 4 x 64 MiB planes (state + ping-pong) vs 126 MiB L2",
                        "vs_baseline_ref": "Table I PyCUDA 14545 Mcell/s at N=4096, Tesla P100 (context)"},
@@ -523,7 +553,7 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
-    ap.add_argument("--leg", choices=("batched", "adjoint", "search"), default=None,
+    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models"), default=None,
                     help="run only this follow-on measurement (small, for profiling) and print it")
     ap.add_argument("--variant", default="temporal", choices=("temporal", "temporal2", "step1", "generic"))
     ap.add_argument("--k", type=int, default=8)
@@ -540,7 +570,8 @@ def main(argv=None):
 
         fn = {"batched": lambda: measure_batched(rd, torch, quick=True),
               "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
-              "search": lambda: measure_search(torch, quick=True)}[args.leg]
+              "search": lambda: measure_search(torch, quick=True),
+              "models": lambda: measure_models(rd, torch)}[args.leg]
         print(json.dumps({"leg": args.leg, **fn()}), flush=True)
         return 0
     return run_ours(args)

@@ -13,6 +13,20 @@
  * an NN x NM torus (indices wrap on both axes, the only boundary of the
  * paper, Sec. II.B-II.C).
  *
+ * The paper presents the simulator as a template for other cellular
+ * nonlinear / FDTD models and names the Chua-Yang cellular neural network
+ * (Sec. I, Sec. II.A) without fixing a second model.  Two such variants are
+ * provided by rdcnn_create / rdcnn_run (forward stepping only):
+ *  - RDCNN_BC_ZEROFLUX: no flux across the grid edge; the ghost cell beyond
+ *    an edge holds the value of the edge cell itself;
+ *  - RDCNN_REACTION_CENN: the Chua-Yang cell with output
+ *    y(x) = (|x + 1| - |x - 1|) / 2, a cross-shaped feedback template
+ *    (centre c, arms Du, corners 0) and a constant offset plane w held in v
+ *    (the control template's response to an input image plus the bias):
+ *      u+_ij = u_ij + dt [ -u_ij + c y(u_ij) + Du (y_{i+1,j} + y_{i-1,j} + y_{i,j-1} + y_{i,j+1}) + v_ij ]
+ *      v+_ij = v_ij
+ *    a, b, eps and Dv are ignored (they must still be finite).
+ *
  * Conventions shared by every entry point
  *  - Layout: one plane per field, row-major [NN][NM], element (i, j) at
  *    offset i * NM + j; i is the row (NN rows), j the column (NM columns).
@@ -59,10 +73,12 @@ enum rdcnn_status {
     RDCNN_ESPACE = -6       /* caller-provided workspace is too small */
 };
 
-enum { RDCNN_BC_PERIODIC = 0 };                   /* toroidal wrap, Sec. II.B-II.C */
+enum { RDCNN_BC_PERIODIC = 0,                    /* toroidal wrap, Sec. II.B-II.C */
+       RDCNN_BC_ZEROFLUX = 1 };                   /* ghost cell = edge cell (see above) */
 enum { RDCNN_F32 = 0, RDCNN_F64 = 1 };
 enum { RDCNN_REACTION_FHN = 0,                    /* Eq. 2-3 */
-       RDCNN_REACTION_NONE = 1 };                 /* f1 = f2 = 0: pure diffusion (testing) */
+       RDCNN_REACTION_NONE = 1,                   /* f1 = f2 = 0: pure diffusion (testing) */
+       RDCNN_REACTION_CENN = 2 };                 /* Chua-Yang cell (see above) */
 enum { RDCNN_VARIANT_AUTO = 0,                    /* library's choice (temporal when possible) */
        RDCNN_VARIANT_STEP1 = 1,                   /* one launch per time step, float4/double2 rows */
        RDCNN_VARIANT_TEMPORAL = 2,                /* k time steps fused per launch */
@@ -82,9 +98,14 @@ typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
 /* ------------------------------------------------------------------ single grid */
 
 /* Create a handle for an NN x NM grid (Sec. II.A: "NNxNM" array of cells).
- * nn, nm >= 1; p finite; boundary = RDCNN_BC_PERIODIC; dtype RDCNN_F32/F64;
- * reaction RDCNN_REACTION_FHN/NONE.  Pure host call (no CUDA work).
- * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL. */
+ * nn, nm >= 1; p finite; boundary RDCNN_BC_PERIODIC/ZEROFLUX; dtype
+ * RDCNN_F32/F64; reaction RDCNN_REACTION_FHN/NONE/CENN.  Du, Dv >= 0 except
+ * for CENN, whose feedback weights c and Du may have either sign (and which
+ * gets no RDCNN_WARN_CFL check).  Pure host call (no CUDA work).
+ * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL.
+ * A ZEROFLUX or CENN handle supports rdcnn_run / rdcnn_run_snapshots with
+ * every variant but RDCNN_VARIANT_TEMPORAL2; rdcnn_adjoint rejects it
+ * (RDCNN_EINVAL). */
 int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p,
                  int boundary, int dtype, int reaction);
 
@@ -126,8 +147,19 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
  * no-op.  Asynchronous on the bound stream.  The vectorised variants need
  * NM to be a multiple of 4 (F32) or 2 (F64) and 16-byte aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns
- * RDCNN_EINVAL.  Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
+ * RDCNN_EINVAL.  The handle's reaction and boundary apply to every variant
+ * except RDCNN_VARIANT_TEMPORAL2, which returns RDCNN_EINVAL for ZEROFLUX
+ * or CENN handles.  Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
 int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k);
+
+/* The launch shape rdcnn_run(h, T, *variant, out->k) would use, without
+ * running anything.  In: *variant (RDCNN_VARIANT_*, AUTO allowed) and
+ * out->k (0 = the handle's tuned or default depth).  Out: *variant resolved
+ * from AUTO, out->k = time steps per full launch (1 for STEP1 / GENERIC),
+ * out->rows = rows per warp strip (the tuned rows, else the launcher's own
+ * choice; 0 for GENERIC).  Queries the current device's SM count and kernel
+ * occupancy.  Errors: RDCNN_EINVAL (as rdcnn_run would return). */
+int rdcnn_plan(const rdcnn_t *h, int *variant, rdcnn_tune *out);
 
 /* Copy the current state out (the "lastA, lastB" the paper's display
  * function returns, Sec. II.A).  to_device = 0: host buffers, the call

@@ -27,10 +27,12 @@ ESTATE = -5
 ESPACE = -6
 
 BC_PERIODIC = 0
+BC_ZEROFLUX = 1
 F32 = 0
 F64 = 1
 REACTION_FHN = 0
 REACTION_NONE = 1
+REACTION_CENN = 2
 VARIANT_AUTO = 0
 VARIANT_STEP1 = 1
 VARIANT_TEMPORAL = 2
@@ -64,6 +66,7 @@ SIGNATURES = [
     ("rdcnn_init", c_int, [c_vp, c_vp, c_double, c_int]),
     ("rdcnn_set_state", c_int, [c_vp, c_vp, c_vp, c_int]),
     ("rdcnn_run", c_int, [c_vp, c_i64, c_int, c_int]),
+    ("rdcnn_plan", c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(Tune)]),
     ("rdcnn_get_state", c_int, [c_vp, c_vp, c_vp, c_int]),
     ("rdcnn_run_snapshots", c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_int, c_vp, c_size]),
     ("rdcnn_destroy", None, [c_vp]),

@@ -35,7 +35,7 @@ def _time(fn, reps: int = 2) -> float:
 
 def tune_grid(grid, x=None, trial_steps: int = 48, force: bool = False) -> dict:
     """Best {variant, k, rows} for this grid's size and dtype (cached)."""
-    key = ("grid", grid.nn, grid.nm, grid.dtype, grid.reaction)
+    key = ("grid", grid.nn, grid.nm, grid.dtype, grid.reaction, getattr(grid, "boundary", "periodic"))
     if key in _cache and not force:
         return dict(_cache[key])
     vec = 4 if grid.dtype == torch.float32 else 2
@@ -44,6 +44,8 @@ def tune_grid(grid, x=None, trial_steps: int = 48, force: bool = False) -> dict:
         _cache[key] = best
         return dict(best)
     cands = GRID_CANDIDATES_F32 if grid.dtype == torch.float32 else GRID_CANDIDATES_F64
+    if getattr(grid, "boundary", "periodic") != "periodic" or grid.reaction == "cenn":
+        cands = [c for c in cands if c[0] != "temporal2"]  # periodic FHN / NONE only
     T = 240 * max(1, trial_steps // 48)  # divisible by every candidate depth
     best = None
     for variant, k, rows in cands:

@@ -379,7 +379,7 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             const int kk = (int)std::min<int64_t>(kf, len - j * kf);
             void *nu = (j == nl - 1) ? (void *)ck_u(i + 1) : (void *)seg_u(j % 2);
             void *nv = (j == nl - 1) ? (void *)ck_v(i + 1) : (void *)seg_v(j % 2);
-            e = launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
+            e = launch_temporal(dtype, reaction, RDCNN_BC_PERIODIC, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
             if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
             cu = nu; cv = nv;
         }
@@ -445,9 +445,11 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
 int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const void *dLdu_T,
                   const void *dLdv_T, int64_t n_checkpoints, void *dLdu0, void *dLdv0,
                   double grad[6], void *workspace, size_t workspace_bytes) {
-    int64_t nn, nm; rdcnn_params p; int dtype, reaction; cudaStream_t s;
-    int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s);
+    int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
+    int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
+    if (boundary != RDCNN_BC_PERIODIC || reaction == RDCNN_REACTION_CENN)
+        return set_error(RDCNN_EINVAL, "the adjoint supports the periodic FHN / NONE models only");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
         return set_error(RDCNN_EINVAL, "NULL argument");

@@ -33,11 +33,12 @@ int cuda_error(cudaError_t e, const char *what) {
     return set_error(RDCNN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int check_params(const rdcnn_params *p) {
+int check_params(const rdcnn_params *p, int reaction) {
     if (!p) return set_error(RDCNN_EINVAL, "params is NULL");
     const double vals[7] = {p->dt, p->a, p->b, p->eps, p->c, p->Du, p->Dv};
     for (double x : vals)
         if (!std::isfinite(x)) return set_error(RDCNN_ENONFINITE, "non-finite gene entry");
+    if (reaction == RDCNN_REACTION_CENN) return RDCNN_OK;  // feedback weights: any sign
     if (p->Du < 0 || p->Dv < 0) return set_error(RDCNN_EINVAL, "diffusion coefficients must be >= 0");
     const double dmax = p->Du > p->Dv ? p->Du : p->Dv;
     if (p->dt * dmax > 0.25) {
@@ -50,10 +51,11 @@ int check_params(const rdcnn_params *p) {
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
-                int *reaction, cudaStream_t *stream) {
+                int *reaction, cudaStream_t *stream, int *boundary) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     *nn = h->nn; *nm = h->nm; *p = h->p; *dtype = h->dtype; *reaction = h->reaction;
     *stream = h->stream;
+    if (boundary) *boundary = h->boundary;
     return RDCNN_OK;
 }
 
@@ -77,22 +79,23 @@ int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p, i
     if (nn < 1 || nm < 1) return set_error(RDCNN_EINVAL, "grid size must be >= 1 (got %lld x %lld)", (long long)nn, (long long)nm);
     if (nn > 0x7fffffff || nm > 0x7fffffff || nn * nm > (int64_t(1) << 40))
         return set_error(RDCNN_EINVAL, "grid too large");
-    if (boundary != RDCNN_BC_PERIODIC) return set_error(RDCNN_EINVAL, "only RDCNN_BC_PERIODIC is supported");
+    if (boundary != RDCNN_BC_PERIODIC && boundary != RDCNN_BC_ZEROFLUX)
+        return set_error(RDCNN_EINVAL, "boundary must be RDCNN_BC_PERIODIC or RDCNN_BC_ZEROFLUX");
     if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "dtype must be RDCNN_F32 or RDCNN_F64");
-    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE)
+    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE && reaction != RDCNN_REACTION_CENN)
         return set_error(RDCNN_EINVAL, "unknown reaction");
-    const int pc = check_params(p);
+    const int pc = check_params(p, reaction);
     if (pc < 0) return pc;
     rdcnn_t *h = new (std::nothrow) rdcnn_t();
     if (!h) return set_error(RDCNN_EINVAL, "out of host memory");
-    h->nn = nn; h->nm = nm; h->p = *p; h->dtype = dtype; h->reaction = reaction;
+    h->nn = nn; h->nm = nm; h->p = *p; h->dtype = dtype; h->reaction = reaction; h->boundary = boundary;
     *out = h;
     return pc;
 }
 
 int rdcnn_set_params(rdcnn_t *h, const rdcnn_params *p) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
-    const int pc = check_params(p);
+    const int pc = check_params(p, h->reaction);
     if (pc < 0) return pc;
     h->p = *p;
     return pc;
@@ -167,6 +170,39 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device) {
 
 namespace rdk {
 
+// Resolve AUTO and the default depth for a run of h; vec_ok says whether the
+// vectorised variants may run (NM multiple of the vector width, aligned
+// buffers).  Returns RDCNN_OK or RDCNN_EINVAL.
+static int resolve_variant(const rdcnn_t *h, bool vec_ok, int *variant, int *k) {
+    if (*variant < RDCNN_VARIANT_AUTO || *variant > RDCNN_VARIANT_TEMPORAL2)
+        return set_error(RDCNN_EINVAL, "unknown variant %d", *variant);
+    if (*variant == RDCNN_VARIANT_AUTO) *variant = vec_ok ? RDCNN_VARIANT_TEMPORAL : RDCNN_VARIANT_GENERIC;
+    if ((*variant == RDCNN_VARIANT_STEP1 || *variant == RDCNN_VARIANT_TEMPORAL ||
+         *variant == RDCNN_VARIANT_TEMPORAL2) && !vec_ok)
+        return set_error(RDCNN_EINVAL,
+                         "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
+                         vec_width(h->dtype));
+    if (*variant == RDCNN_VARIANT_TEMPORAL2 &&
+        (h->boundary != RDCNN_BC_PERIODIC || h->reaction == RDCNN_REACTION_CENN))
+        return set_error(RDCNN_EINVAL, "RDCNN_VARIANT_TEMPORAL2 supports the periodic FHN / NONE models only");
+    if (*variant == RDCNN_VARIANT_TEMPORAL || *variant == RDCNN_VARIANT_TEMPORAL2) {
+        if (*k == 0) *k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
+        if (*k < 1 || *k > max_k(h->dtype))
+            return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(h->dtype));
+    } else {
+        *k = 1;
+    }
+    return RDCNN_OK;
+}
+
+static bool vec_ok_for(const rdcnn_t *h) {
+    const bool nm_ok = (h->nm % vec_width(h->dtype) == 0);
+    if (!h->bound) return nm_ok;
+    const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
+    const char *ws = (const char *)h->ws;
+    return nm_ok && aligned16(h->u) && aligned16(h->v) && aligned16(ws) && aligned16(ws + plane);
+}
+
 int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
@@ -177,21 +213,8 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
     char *ws = (char *)h->ws;
     void *su = ws, *sv = ws + plane;
-    const bool vec_ok = (h->nm % vec_width(h->dtype) == 0) && aligned16(h->u) && aligned16(h->v) &&
-                        aligned16(su) && aligned16(sv);
-    if (variant == RDCNN_VARIANT_AUTO) variant = vec_ok ? RDCNN_VARIANT_TEMPORAL : RDCNN_VARIANT_GENERIC;
-    if ((variant == RDCNN_VARIANT_STEP1 || variant == RDCNN_VARIANT_TEMPORAL ||
-         variant == RDCNN_VARIANT_TEMPORAL2) && !vec_ok)
-        return set_error(RDCNN_EINVAL,
-                         "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
-                         vec_width(h->dtype));
-    if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2) {
-        if (k == 0) k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
-        if (k < 1 || k > max_k(h->dtype))
-            return set_error(RDCNN_EINVAL, "k must be in 1..%d", max_k(h->dtype));
-    } else {
-        k = 1;
-    }
+    const int rv = resolve_variant(h, vec_ok_for(h), &variant, &k);
+    if (rv < 0) return rv;
     const void *cu = h->u, *cv = h->v;
     void *nu = su, *nv = sv;
     int64_t left = T;
@@ -204,14 +227,15 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
             e = launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
                                       h->tune_rows, h->stream);  // 0 = chosen by the launcher
         else if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
-            e = launch_temporal(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
-                                h->tune_rows, h->stream);  // 0 = chosen by the launcher
+            e = launch_temporal(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm,
+                                h->p, h->tune_rows, h->stream);  // 0 = chosen by the launcher
         else if (variant == RDCNN_VARIANT_STEP1)
-            e = launch_step1(h->dtype, h->reaction, cu, cv, nu, nv, h->nn, h->nm, h->p,
+            e = launch_step1(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p,
                              h->tune_rows ? h->tune_rows : default_rows_step1(h->dtype, h->nn, h->nm),
                              h->stream);
         else
-            e = launch_generic(h->dtype, h->reaction, cu, cv, nu, nv, h->nn, h->nm, h->p, h->stream);
+            e = launch_generic(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                               h->stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel launch");
         const void *tu = cu, *tv = cv;
         cu = nu; cv = nv;
@@ -235,6 +259,18 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
 extern "C" {
 
 int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) { return run_core(h, T, variant, k, 0, nullptr, nullptr); }
+
+int rdcnn_plan(const rdcnn_t *h, int *variant, rdcnn_tune *out) {
+    if (!h || !variant || !out) return set_error(RDCNN_EINVAL, "NULL argument");
+    int v = *variant, k = out->k;
+    const int rv = resolve_variant(h, vec_ok_for(h), &v, &k);
+    if (rv < 0) return rv;
+    const int rows = v == RDCNN_VARIANT_GENERIC ? 0 : h->tune_rows;
+    out->rows = plan_rows(h->dtype, h->reaction, h->boundary, v, k, h->nn, h->nm, rows);
+    out->k = k;
+    *variant = v;
+    return RDCNN_OK;
+}
 
 int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");

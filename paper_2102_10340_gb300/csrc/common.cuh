@@ -1,14 +1,17 @@
 // common.cuh -- device-side building blocks shared by the RD-CNN kernels.
 //
 // The cell update is Eq. 1 of Sec. II.A with the FitzHugh-Nagumo terms of
-// Eq. 2-3.  Every kernel of the library (single step, temporally blocked,
-// batched) computes a cell through fhn_cell() below, and fhn_cell() spells
-// out each rounding with the *_rn intrinsics, so the compiler cannot contract
-// or reorder differently in different kernels: all variants give bit-identical
-// states for the same inputs.
+// Eq. 2-3, or one of the other local models the simulator is a template for
+// (Sec. I, Sec. II.A): pure diffusion, and the Chua-Yang cellular neural
+// network cell.  Every kernel of the library (single step, temporally
+// blocked, batched) computes a cell through cell_update() below, and
+// cell_update() spells out each rounding with the *_rn intrinsics, so the
+// compiler cannot contract or reorder differently in different kernels: all
+// variants give bit-identical states for the same inputs.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "rdcnn.h"
@@ -17,7 +20,31 @@ namespace rdk {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-enum { RX_FHN = 0, RX_NONE = 1 };
+// Local model (values equal to RDCNN_REACTION_*).
+enum { RX_FHN = 0, RX_NONE = 1, RX_CENN = 2 };
+
+// Boundary (values equal to RDCNN_BC_*): wrap = torus; mirror = zero flux,
+// the ghost cell beyond an edge holds the edge cell's value.
+enum { BC_WRAP = 0, BC_MIRROR = 1 };
+
+template <int N> using IntC = std::integral_constant<int, N>;
+
+// Host-side dispatch of a runtime (reaction, boundary) pair to a callable
+// taking the two as compile-time tags: f(IntC<RX>{}, IntC<BC>{}).
+template <class F>
+inline cudaError_t with_model(int reaction, int boundary, F &&f) {
+    const bool zf = (boundary == RDCNN_BC_ZEROFLUX);
+    switch (reaction) {
+        case RDCNN_REACTION_FHN:
+            return zf ? f(IntC<RX_FHN>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_FHN>{}, IntC<BC_WRAP>{});
+        case RDCNN_REACTION_NONE:
+            return zf ? f(IntC<RX_NONE>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_NONE>{}, IntC<BC_WRAP>{});
+        case RDCNN_REACTION_CENN:
+            return zf ? f(IntC<RX_CENN>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_CENN>{}, IntC<BC_WRAP>{});
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
 
 // 16-byte vector of the element type: the unit each lane loads and stores.
 template <typename T> struct Vec;
@@ -35,6 +62,7 @@ template <> struct Vec<double> {
 // ebm4 = eps b - 4 Dv); the state itself always enters the final FMA
 // exactly, so only increment-sized terms carry coefficient rounding.
 // With no reaction: cm4 = -4 Du, ebm4 = -4 Dv, mthird = meps = mepsa = 0.
+// CeNN cell: cm4 = c (feedback centre), Du = feedback arms, the rest 0.
 template <typename T> struct Coef {
     T dt, Du, Dv, cm4, mthird, meps, ebm4, mepsa;
 };
@@ -46,18 +74,32 @@ __device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(
 __device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
 __device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
 
-// One cell of Eq. 1.  c* = centre, n/s = rows i-1/i+1, w/e = columns j-1/j+1.
-// Evaluated as
+__device__ __forceinline__ float clamp1(float x) { return fminf(fmaxf(x, -1.0f), 1.0f); }
+__device__ __forceinline__ double clamp1(double x) { return fmin(fmax(x, -1.0), 1.0); }
+
+// One cell.  c* = centre, n/s = rows i-1/i+1, w/e = columns j-1/j+1.
+// FitzHugh-Nagumo (Eq. 1-3) is evaluated as
 //   u+ = u + dt [ Du ((n + s) + (w + e)) + u (c - 4 Du - u^2/3) - v ]
 //   v+ = v + dt [ Dv ((n + s) + (w + e)) - eps u + (eps b - 4 Dv) v - eps a ]
-// i.e. Eq. 1-3 with the -4 Du u (-4 Dv v) term of the Laplacian moved into
-// the reaction polynomial: 15 FP instructions per cell instead of 18.  The
-// state is the exact addend of the last FMA, so the FP32 accuracy is that of
-// the literal form.
+// i.e. with the -4 Du u (-4 Dv v) term of the Laplacian moved into the
+// reaction polynomial: 15 FP instructions per cell instead of 18.  The state
+// is the exact addend of the last FMA, so the FP32 accuracy is that of the
+// literal form.
+// CeNN (Chua-Yang cell, output y(x) = clamp(x, -1, 1), which equals
+// (|x + 1| - |x - 1|) / 2; u = state x, v = offset plane w, held constant):
+//   u+ = u + dt [ Du ((y_n + y_s) + (y_w + y_e)) + c y(u) + (w - u) ],  v+ = v.
+// A NaN state stays NaN (it is the exact addend); a NaN neighbour's output
+// saturates to -1 instead of propagating.
 template <typename T, int RX>
-__device__ __forceinline__ void fhn_cell(T uc, T un, T us, T uw, T ue,
-                                         T vc, T vn, T vs, T vw, T ve,
-                                         const Coef<T> &p, T &out_u, T &out_v) {
+__device__ __forceinline__ void cell_update(T uc, T un, T us, T uw, T ue,
+                                            T vc, T vn, T vs, T vw, T ve,
+                                            const Coef<T> &p, T &out_u, T &out_v) {
+    if constexpr (RX == RX_CENN) {
+        const T sy = add_rn(add_rn(clamp1(un), clamp1(us)), add_rn(clamp1(uw), clamp1(ue)));
+        out_u = fma_rn(p.dt, fma_rn(p.Du, sy, fma_rn(p.cm4, clamp1(uc), add_rn(vc, -uc))), uc);
+        out_v = vc;
+        return;
+    }
     const T su = add_rn(add_rn(un, us), add_rn(uw, ue));      // neighbour sum of u
     const T sv = add_rn(add_rn(vn, vs), add_rn(vw, ve));      // neighbour sum of v
     T ru, rv;
@@ -118,7 +160,7 @@ __device__ __forceinline__ void slice_update(const Slice<T> &nor, const Slice<T>
         const T eu = (e == V - 1) ? east_u : cen.u[e + 1];
         const T wv = (e == 0) ? west_v : cen.v[e - 1];
         const T ev = (e == V - 1) ? east_v : cen.v[e + 1];
-        fhn_cell<T, RX>(cen.u[e], nor.u[e], sou.u[e], wu, eu,
+        cell_update<T, RX>(cen.u[e], nor.u[e], sou.u[e], wu, eu,
                         cen.v[e], nor.v[e], sou.v[e], wv, ev, p, out.u[e], out.v[e]);
     }
 }
@@ -127,6 +169,14 @@ template <typename T>
 inline Coef<T> make_coef(const rdcnn_params &p, int reaction) {
     const bool fhn = (reaction == RDCNN_REACTION_FHN);
     Coef<T> q;
+    if (reaction == RDCNN_REACTION_CENN) {
+        q.dt = T(p.dt);
+        q.Du = T(p.Du);
+        q.Dv = T(0);
+        q.cm4 = T(p.c);
+        q.mthird = q.meps = q.ebm4 = q.mepsa = T(0);
+        return q;
+    }
     q.dt = T(p.dt);
     q.Du = T(p.Du);
     q.Dv = T(p.Dv);
@@ -157,6 +207,19 @@ __device__ __forceinline__ void zero_slice(Slice<T> &s) {
 __device__ __forceinline__ int wrap_row(int64_t r, int64_t n) {
     int64_t q = r % n;
     return (int)(q < 0 ? q + n : q);
+}
+
+// Index that stands in for row/column r under boundary BC: wrapped modulo n
+// on the torus; under zero flux, reflected about the edge faces (r = -1 -> 0,
+// r = n -> n - 1, and periodically with period 2n beyond that).
+template <int BC>
+__device__ __forceinline__ int bc_index(int64_t r, int64_t n) {
+    if constexpr (BC == BC_MIRROR) {
+        const int q = wrap_row(r, 2 * n);
+        return q < n ? q : (int)(2 * n - 1 - q);
+    } else {
+        return wrap_row(r, n);
+    }
 }
 
 }  // namespace rdk

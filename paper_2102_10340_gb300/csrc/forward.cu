@@ -18,8 +18,12 @@
 //              values after K steps and do not store.
 //  k_generic   one thread per cell, scalar loads: any size and alignment.
 //
-// All three evaluate cells with rdk::fhn_cell, so they produce identical
-// bits for identical inputs.
+// All three evaluate cells with rdk::cell_update, so they produce identical
+// bits for identical inputs.  Under the zero-flux boundary the single-step
+// and generic kernels clamp neighbour indices into the grid (the ghost cell
+// is the edge cell); the temporal kernel loads mirrored halos instead
+// (temporal.cuh).  k_temporal's launchers live in temporal_launch.cuh and are
+// instantiated in the temporal_*.cu units, which compile in parallel.
 #include <algorithm>
 
 #include "common.cuh"
@@ -35,11 +39,12 @@ constexpr int kStep1Block = 256;
 
 // --------------------------------------------------------------------------- single step
 
-template <typename T, int RX>
+template <typename T, int RX, int BC>
 __global__ void __launch_bounds__(kStep1Block)
 k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
         T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
     constexpr int V = Vec<T>::N;
+    constexpr bool zf = (BC == BC_MIRROR);
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * (kStep1Block / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;  // whole warps only
@@ -47,8 +52,9 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
     const int strip = wid / bands;
     const int col = band * 32 * V + lane * V;
     const bool active = col < nm;
-    const int colw = (col == 0) ? nm - 1 : col - 1;
-    const int cole = (col + V >= nm) ? 0 : col + V;
+    // neighbour columns beyond the edges: wrapped, or the edge cell itself
+    const int colw = (col == 0) ? (zf ? 0 : nm - 1) : col - 1;
+    const int cole = (col + V >= nm) ? (zf ? nm - 1 : 0) : col + V;
     const bool edge_w = (lane == 0);
     const bool edge_e = active && (lane == 31 || col + V >= nm);
     const int r0 = strip * rows;
@@ -60,9 +66,9 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
     T pw_u = 0, pe_u = 0, pw_v = 0, pe_v = 0;  // ... of row "pre"
     zero_slice(nor); zero_slice(cen); zero_slice(sou); zero_slice(pre);
 
-    int rn = (r0 == 0) ? nn - 1 : r0 - 1;
+    int rn = (r0 == 0) ? (zf ? 0 : nn - 1) : r0 - 1;
     int rc = r0;
-    int rs = (r0 + 1 == nn) ? 0 : r0 + 1;
+    int rs = (r0 + 1 == nn) ? (zf ? nn - 1 : 0) : r0 + 1;
     if (active) {
         load_slice(nor, u, v, (int64_t)rn * nm + col);
         load_slice(cen, u, v, (int64_t)rc * nm + col);
@@ -80,7 +86,7 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
     for (int r = r0; r < r1; ++r) {
         // prefetch row r+2 (wrapped) while row r is computed
         const bool more = (r + 1 < r1);
-        const int rp = (rs + 1 == nn) ? 0 : rs + 1;
+        const int rp = (rs + 1 == nn) ? (zf ? nn - 1 : 0) : rs + 1;
         if (more) {
             if (active) load_slice(pre, u, v, (int64_t)rp * nm + col);
             if (edge_w) { pw_u = __ldg(u + (int64_t)rp * nm + colw); pw_v = __ldg(v + (int64_t)rp * nm + colw); }
@@ -121,25 +127,26 @@ k_temporal_split(const T *__restrict__ u, const T *__restrict__ v, T *__restrict
 
 // --------------------------------------------------------------------------- generic
 
-template <typename T, int RX>
+template <typename T, int RX, int BC>
 __global__ void __launch_bounds__(256)
 k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
           T *__restrict__ vn, int nn, int nm, Coef<T> p) {
+    constexpr bool zf = (BC == BC_MIRROR);
     const int64_t n = (int64_t)nn * nm;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx / nm);
         const int j = (int)(idx - (int64_t)i * nm);
-        const int ip = (i + 1 == nn) ? 0 : i + 1;
-        const int im = (i == 0) ? nn - 1 : i - 1;
-        const int jp = (j + 1 == nm) ? 0 : j + 1;
-        const int jm = (j == 0) ? nm - 1 : j - 1;
+        const int ip = (i + 1 == nn) ? (zf ? i : 0) : i + 1;
+        const int im = (i == 0) ? (zf ? 0 : nn - 1) : i - 1;
+        const int jp = (j + 1 == nm) ? (zf ? j : 0) : j + 1;
+        const int jm = (j == 0) ? (zf ? 0 : nm - 1) : j - 1;
         const int64_t ri = (int64_t)i * nm;
         const int64_t rp = (int64_t)ip * nm;
         const int64_t rm = (int64_t)im * nm;
         T ou, ov;
-        fhn_cell<T, RX>(u[ri + j], u[rm + j], u[rp + j], u[ri + jm], u[ri + jp],
-                        v[ri + j], v[rm + j], v[rp + j], v[ri + jm], v[ri + jp], p, ou, ov);
+        cell_update<T, RX>(u[ri + j], u[rm + j], u[rp + j], u[ri + jm], u[ri + jp],
+                           v[ri + j], v[rm + j], v[rp + j], v[ri + jm], v[ri + jp], p, ou, ov);
         un[idx] = ou;
         vn[idx] = ov;
     }
@@ -157,8 +164,8 @@ k_init(const T *__restrict__ x, T *u, T *v, T ka, int64_t n) {
 }
 
 template <typename T>
-cudaError_t step1_t(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
-                    int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
+cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, void *un, void *vn,
+                    int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
     constexpr int V = Vec<T>::N;
     const int bands = (int)((nm + 32 * V - 1) / (32 * V));
     const int strips = (int)((nn + rows - 1) / rows);
@@ -166,17 +173,15 @@ cudaError_t step1_t(int reaction, const void *u, const void *v, void *un, void *
     const int wpb = kStep1Block / 32;
     const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
     const Coef<T> c = make_coef<T>(p, reaction);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_step1<T, RX_FHN><<<grid, kStep1Block, 0, s>>>((const T *)u, (const T *)v, (T *)un,
-                                                        (T *)vn, (int)nn, (int)nm, bands,
-                                                        (int)nwarps, rows, c);
-    else
-        k_step1<T, RX_NONE><<<grid, kStep1Block, 0, s>>>((const T *)u, (const T *)v, (T *)un,
-                                                         (T *)vn, (int)nn, (int)nm, bands,
-                                                         (int)nwarps, rows, c);
-    count_launches(1);
-    return cudaGetLastError();
+    return with_model(reaction, boundary, [&](auto rx, auto bc) {
+        k_step1<T, decltype(rx)::value, decltype(bc)::value><<<grid, kStep1Block, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, rows, c);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
+
+}  // namespace
 
 // Rows per warp strip when the caller gives none.  Small grids use short
 // strips (few warps exist at all); large grids pick, among a few lengths,
@@ -203,47 +208,7 @@ int auto_rows_temporal(int K, int64_t nn, int64_t nm, int bands, int blocks_per_
     return best;
 }
 
-template <typename T, int K, int RX>
-int temporal_blocks_per_sm() {
-    static int cached = -1;
-    if (cached < 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_temporal<T, K, RX>, kTemporalBlock, 0) !=
-            cudaSuccess)
-            nb = 1;
-        cached = nb;
-    }
-    return cached;
-}
-
-template <typename T, int K>
-cudaError_t temporal_tk(int reaction, const void *u, const void *v, void *un, void *vn,
-                        int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
-    constexpr int V = Vec<T>::N;
-    constexpr int H = (K + V - 1) / V;
-    constexpr int OUTW = (32 - 2 * H) * V;
-    const int bands = (int)((nm + OUTW - 1) / OUTW);
-    if (rows <= 0) {
-        const int bps = reaction == RDCNN_REACTION_FHN ? temporal_blocks_per_sm<T, K, RX_FHN>()
-                                                       : temporal_blocks_per_sm<T, K, RX_NONE>();
-        rows = auto_rows_temporal(K, nn, nm, bands, bps, kTemporalBlock / 32);
-    }
-    const int strips = (int)((nn + rows - 1) / rows);
-    const int64_t nwarps = (int64_t)bands * strips;
-    const int wpb = kTemporalBlock / 32;
-    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    const Coef<T> c = make_coef<T>(p, reaction);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_temporal<T, K, RX_FHN><<<grid, kTemporalBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps,
-            rows, c);
-    else
-        k_temporal<T, K, RX_NONE><<<grid, kTemporalBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps,
-            rows, c);
-    count_launches(1);
-    return cudaGetLastError();
-}
+namespace {
 
 template <typename T, int K, int RX>
 int split_blocks_per_sm() {
@@ -259,17 +224,25 @@ int split_blocks_per_sm() {
 }
 
 template <typename T, int K>
+int split_rows(int reaction, int64_t nn, int64_t nm, int rows) {
+    if (rows > 0) return rows;
+    constexpr int V = Vec<T>::N;
+    constexpr int H = (K + V - 1) / V;
+    constexpr int OUTW = (32 - 2 * H) * V;
+    const int bands = (int)((nm + OUTW - 1) / OUTW);
+    const int bps = reaction == RDCNN_REACTION_FHN ? split_blocks_per_sm<T, K, RX_FHN>()
+                                                   : split_blocks_per_sm<T, K, RX_NONE>();
+    return auto_rows_temporal(K, nn, nm, bands, bps, kSplitPairs);
+}
+
+template <typename T, int K>
 cudaError_t split_tk(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
                      int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
     constexpr int V = Vec<T>::N;
     constexpr int H = (K + V - 1) / V;
     constexpr int OUTW = (32 - 2 * H) * V;
     const int bands = (int)((nm + OUTW - 1) / OUTW);
-    if (rows <= 0) {
-        const int bps = reaction == RDCNN_REACTION_FHN ? split_blocks_per_sm<T, K, RX_FHN>()
-                                                       : split_blocks_per_sm<T, K, RX_NONE>();
-        rows = auto_rows_temporal(K, nn, nm, bands, bps, kSplitPairs);
-    }
+    rows = split_rows<T, K>(reaction, nn, nm, rows);
     const int strips = (int)((nn + rows - 1) / rows);
     const int64_t nitems = (int64_t)bands * strips;
     const unsigned grid = (unsigned)((nitems + kSplitPairs - 1) / kSplitPairs);
@@ -285,20 +258,18 @@ cudaError_t split_tk(int reaction, const void *u, const void *v, void *un, void 
 }
 
 template <typename T>
-cudaError_t generic_t(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
-                      int64_t nm, const rdcnn_params &p, cudaStream_t s) {
+cudaError_t generic_t(int reaction, int boundary, const void *u, const void *v, void *un, void *vn,
+                      int64_t nn, int64_t nm, const rdcnn_params &p, cudaStream_t s) {
     const int64_t n = nn * nm;
     const int64_t want = (n + 255) / 256;
     const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)sm_count() * 16);
     const Coef<T> c = make_coef<T>(p, reaction);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_generic<T, RX_FHN><<<grid, 256, 0, s>>>((const T *)u, (const T *)v, (T *)un, (T *)vn,
-                                                  (int)nn, (int)nm, c);
-    else
-        k_generic<T, RX_NONE><<<grid, 256, 0, s>>>((const T *)u, (const T *)v, (T *)un, (T *)vn,
-                                                   (int)nn, (int)nm, c);
-    count_launches(1);
-    return cudaGetLastError();
+    return with_model(reaction, boundary, [&](auto rx, auto bc) {
+        k_generic<T, decltype(rx)::value, decltype(bc)::value><<<grid, 256, 0, s>>>(
+            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, c);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace
@@ -311,41 +282,45 @@ int sm_count() {
     return 152;
 }
 
-cudaError_t launch_step1(int dtype, int reaction, const void *u, const void *v, void *un,
-                         void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
+cudaError_t launch_step1(int dtype, int reaction, int boundary, const void *u, const void *v,
+                         void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
                          cudaStream_t s) {
-    if (dtype == RDCNN_F64) return step1_t<double>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-    return step1_t<float>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+    if (dtype == RDCNN_F64) return step1_t<double>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+    return step1_t<float>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
 }
 
-cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const void *v,
-                            void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
-                            int rows, cudaStream_t s) {
+cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const void *u,
+                            const void *v, void *un, void *vn, int64_t nn, int64_t nm,
+                            const rdcnn_params &p, int rows, cudaStream_t s) {
+#define RDK_TL(TT, KK) temporal_launch<TT, KK>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s)
     if (dtype == RDCNN_F64) {
         switch (k) {
-            case 1: return temporal_tk<double, 1>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            case 2: return temporal_tk<double, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            case 3: return temporal_tk<double, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            case 4: return temporal_tk<double, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            case 1: return RDK_TL(double, 1);
+            case 2: return RDK_TL(double, 2);
+            case 3: return RDK_TL(double, 3);
+            case 4: return RDK_TL(double, 4);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (k) {
-        case 1: return temporal_tk<float, 1>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 2: return temporal_tk<float, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 3: return temporal_tk<float, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 4: return temporal_tk<float, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 5: return temporal_tk<float, 5>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 6: return temporal_tk<float, 6>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 7: return temporal_tk<float, 7>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 8: return temporal_tk<float, 8>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+        case 1: return RDK_TL(float, 1);
+        case 2: return RDK_TL(float, 2);
+        case 3: return RDK_TL(float, 3);
+        case 4: return RDK_TL(float, 4);
+        case 5: return RDK_TL(float, 5);
+        case 6: return RDK_TL(float, 6);
+        case 7: return RDK_TL(float, 7);
+        case 8: return RDK_TL(float, 8);
         default: return cudaErrorInvalidValue;
     }
+#undef RDK_TL
 }
 
+// Periodic FitzHugh-Nagumo / pure diffusion only (the caller checks).
 cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                                   int rows, cudaStream_t s) {
+    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE) return cudaErrorInvalidValue;
     if (dtype == RDCNN_F64) {
         switch (k) {
             case 2: return split_tk<double, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
@@ -366,11 +341,11 @@ cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u,
     }
 }
 
-cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v, void *un,
-                           void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+cudaError_t launch_generic(int dtype, int reaction, int boundary, const void *u, const void *v,
+                           void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                            cudaStream_t s) {
-    if (dtype == RDCNN_F64) return generic_t<double>(reaction, u, v, un, vn, nn, nm, p, s);
-    return generic_t<float>(reaction, u, v, un, vn, nn, nm, p, s);
+    if (dtype == RDCNN_F64) return generic_t<double>(reaction, boundary, u, v, un, vn, nn, nm, p, s);
+    return generic_t<float>(reaction, boundary, u, v, un, vn, nn, nm, p, s);
 }
 
 cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
@@ -383,6 +358,42 @@ cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, i
         k_init<float><<<grid, 256, 0, s>>>((const float *)x, (float *)u, (float *)v, (float)ka, n);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <typename T, int K>
+int plan_rows_k(int reaction, int boundary, int variant, int64_t nn, int64_t nm, int rows) {
+    if constexpr (K >= 2) {
+        if (variant == RDCNN_VARIANT_TEMPORAL2) return split_rows<T, K>(reaction, nn, nm, rows);
+    }
+    return temporal_rows<T, K>(reaction, boundary, nn, nm, rows);
+}
+
+int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t nn, int64_t nm,
+              int rows) {
+    if (variant == RDCNN_VARIANT_STEP1) return rows > 0 ? rows : default_rows_step1(dtype, nn, nm);
+    if (variant == RDCNN_VARIANT_GENERIC) return 0;
+#define RDK_PR(TT, KK) plan_rows_k<TT, KK>(reaction, boundary, variant, nn, nm, rows)
+    if (dtype == RDCNN_F64) {
+        switch (k) {
+            case 1: return RDK_PR(double, 1);
+            case 2: return RDK_PR(double, 2);
+            case 3: return RDK_PR(double, 3);
+            case 4: return RDK_PR(double, 4);
+            default: return 0;
+        }
+    }
+    switch (k) {
+        case 1: return RDK_PR(float, 1);
+        case 2: return RDK_PR(float, 2);
+        case 3: return RDK_PR(float, 3);
+        case 4: return RDK_PR(float, 4);
+        case 5: return RDK_PR(float, 5);
+        case 6: return RDK_PR(float, 6);
+        case 7: return RDK_PR(float, 7);
+        case 8: return RDK_PR(float, 8);
+        default: return 0;
+    }
+#undef RDK_PR
 }
 
 // Temporal depth by grid size, from a launch-shape sweep on GB300 (FP32,

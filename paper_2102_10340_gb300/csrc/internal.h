@@ -13,6 +13,7 @@ struct rdcnn {
     rdcnn_params p{};
     int dtype = RDCNN_F32;
     int reaction = RDCNN_REACTION_FHN;
+    int boundary = RDCNN_BC_PERIODIC;
     void *u = nullptr, *v = nullptr, *ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -43,15 +44,17 @@ void count_launches(uint64_t n);
 // Error reporting (thread-local message, returned code passes through).
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
-// Validates a gene: RDCNN_OK, RDCNN_WARN_CFL, or a negative code.
-int check_params(const rdcnn_params *p);
+// Validates a gene for a reaction: RDCNN_OK, RDCNN_WARN_CFL, or a negative
+// code.  The CeNN cell takes feedback weights of either sign in Du and c and
+// has no diffusion stability bound.
+int check_params(const rdcnn_params *p, int reaction = RDCNN_REACTION_FHN);
 bool aligned16(const void *p);
 int sm_count();
 
 // Read-only view of a handle's configuration (defined in api.cu); the stream
 // is the one bound by rdcnn_bind (NULL if unbound).
 int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
-                int *reaction, cudaStream_t *stream);
+                int *reaction, cudaStream_t *stream, int *boundary = nullptr);
 
 // Callback of run_core: called after the launch that completes step t (a
 // multiple of `every`), with the planes that hold the state at that step.
@@ -63,20 +66,39 @@ typedef int (*MarkFn)(void *ctx, int64_t t, const void *cu, const void *cv);
 int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx);
 
 // Kernel launchers.  All return the launch status (cudaGetLastError()).
-// u/v are read, un/vn written; the two pairs must not overlap.
-cudaError_t launch_step1(int dtype, int reaction, const void *u, const void *v, void *un,
-                         void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
+// u/v are read, un/vn written; the two pairs must not overlap.  reaction is
+// an RDCNN_REACTION_*, boundary an RDCNN_BC_*.
+cudaError_t launch_step1(int dtype, int reaction, int boundary, const void *u, const void *v,
+                         void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
                          cudaStream_t s);
-cudaError_t launch_temporal(int dtype, int reaction, int k, const void *u, const void *v,
-                            void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
-                            int rows, cudaStream_t s);
-// The temporal pipeline with the K stages split across a warp pair (k >= 2).
+cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const void *u,
+                            const void *v, void *un, void *vn, int64_t nn, int64_t nm,
+                            const rdcnn_params &p, int rows, cudaStream_t s);
+// The temporal pipeline with the K stages split across a warp pair (k >= 2);
+// periodic boundary, FitzHugh-Nagumo or no reaction.
 cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                                   int rows, cudaStream_t s);
-cudaError_t launch_generic(int dtype, int reaction, const void *u, const void *v, void *un,
-                           void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
+cudaError_t launch_generic(int dtype, int reaction, int boundary, const void *u, const void *v,
+                           void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                            cudaStream_t s);
+// One depth of the temporal kernel (temporal_launch.cuh; instantiated for
+// float K = 1..8 and double K = 1..4 in the temporal_*.cu units).
+template <typename T, int K>
+cudaError_t temporal_launch(int reaction, int boundary, const void *u, const void *v, void *un,
+                            void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
+                            cudaStream_t s);
+// Rows per warp strip a temporal launch of depth K uses for the requested
+// rows (rows <= 0: the launcher's own choice).
+template <typename T, int K>
+int temporal_rows(int reaction, int boundary, int64_t nn, int64_t nm, int rows);
+// The same for every launcher: rows per warp (or per warp pair) of a launch
+// of `variant` (an RDCNN_VARIANT_*, already resolved from AUTO) at depth k.
+int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t nn, int64_t nm,
+              int rows);
+// Rows per warp strip of a temporal launch (wave-quantisation model).
+int auto_rows_temporal(int K, int64_t nn, int64_t nm, int bands, int blocks_per_sm,
+                       int warps_per_block);
 // u = v = ka * x; x may alias u.
 cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
                         cudaStream_t s);

@@ -100,8 +100,8 @@ int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, i
     for (int64_t left = T; left > 0;) {
         const int kk = vec ? (int)(left < k ? left : k) : 1;
         const cudaError_t e =
-            vec ? launch_temporal(dtype, reaction, kk, cu, cv, nu, nv, nn, nm, *p, 0, s)
-                : launch_generic(dtype, reaction, cu, cv, nu, nv, nn, nm, *p, s);
+            vec ? launch_temporal(dtype, reaction, RDCNN_BC_PERIODIC, kk, cu, cv, nu, nv, nn, nm, *p, 0, s)
+                : launch_generic(dtype, reaction, RDCNN_BC_PERIODIC, cu, cv, nu, nv, nn, nm, *p, s);
         if (e != cudaSuccess) return cuda_error(e, "static-scratch step launch");
         const void *tu = cu, *tv = cv;
         cu = nu; cv = nv;

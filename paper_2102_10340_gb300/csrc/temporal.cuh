@@ -11,6 +11,17 @@
 // stage s turns rows (q-1, q, q+1)
 // of stage s-1 into row q of stage s.  After K stages the K outermost columns
 // on each side are stale, which is why only lanes H .. 31-H store.
+//
+// Zero-flux boundary (BC_MIRROR): the halo rows and columns beyond a grid
+// edge are loaded as the mirror image of the rows and columns inside it
+// (row -1 <- row 0, row -2 <- row 1, ...; a lane whose 16-byte vector lies
+// beyond an edge loads the mirrored vector and reverses its elements).  The
+// 2N x 2M torus holding that mirror image evolves exactly like the zero-flux
+// grid (the edge faces are mirror planes and the update keeps a mirrored
+// state mirrored), so every stage sees the edge cell as its own outside
+// neighbour with no per-stage test; only the input indexing differs.  Sums
+// of mirrored pairs are formed in swapped order, which IEEE addition does not
+// notice: the results are the bits the single-step kernel computes.
 #pragma once
 
 #include "common.cuh"
@@ -61,6 +72,49 @@ __device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<T> &
     }
 }
 
+// ring_read for boundary BC; under BC_MIRROR a lane whose columns lie beyond
+// an edge (rev) reverses the element order of the mirrored vector it loaded.
+template <typename T, int BC>
+__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<T> &s) {
+    ring_read(r, m, s);
+    if constexpr (BC == BC_MIRROR) {
+        constexpr int V = Vec<T>::N;
+        Slice<T> t = s;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            s.u[e] = rev ? t.u[V - 1 - e] : t.u[e];
+            s.v[e] = rev ? t.v[V - 1 - e] : t.v[e];
+        }
+    }
+}
+
+// Source row of the strip's input rows, advanced one row per beat: wrapped
+// on the torus; under zero flux the reflected sequence (..., 1, 0, 0, 1, ...
+// at the top edge, ..., n-2, n-1, n-1, n-2, ... at the bottom).
+template <int BC> struct RowWalk {
+    int g = 0, dir = 1;
+    __device__ __forceinline__ void start(int64_t r, int n) {
+        if constexpr (BC == BC_MIRROR) {
+            const int q = wrap_row(r, 2 * (int64_t)n);
+            g = q < n ? q : 2 * n - 1 - q;
+            dir = q < n ? 1 : -1;
+        } else {
+            g = wrap_row(r, n);
+        }
+    }
+    __device__ __forceinline__ void next(int n) {
+        if constexpr (BC == BC_MIRROR) {
+            if (dir > 0) {
+                if (g == n - 1) dir = -1; else ++g;
+            } else {
+                if (g == 0) dir = 1; else --g;
+            }
+        } else {
+            g = (g + 1 == n) ? 0 : g + 1;
+        }
+    }
+};
+
 // One pipeline beat: take input row m of the strip from the ring (issuing the
 // copy of row m + kRing - 1 first), advance every stage by one row, and hand
 // the finished row (stage K) to the policy.  W[PH], W[PH+1] hold the two older
@@ -75,24 +129,24 @@ __device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<T> &
 //        stage s maps rows q-1 (A), q (B), q+1 (C) of its input to row q of
 //        its output (q = input-row index within the strip, see temporal_strip)
 //   P::finish(q, out)                    the row q leaving the last stage
-template <typename T, int K, int PH, class P>
+template <typename T, int K, int PH, int BC, class P>
 __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<T> (&W)[3][K],
-                                              const RowRing<T> &ring, int &g_issue, int nn, int nm,
-                                              int lc, const T *__restrict__ u, const T *__restrict__ v,
-                                              P &pol) {
+                                              const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
+                                              int lc, bool rev, const T *__restrict__ u,
+                                              const T *__restrict__ v, P &pol) {
     constexpr int V = Vec<T>::N;
     if (m >= total) return;
     // The slot written here was read in the previous beat, whose stage
     // computations (issued before this point) consumed that value.
     if (m + kRing - 1 < total) {
-        ring_issue(ring, m + kRing - 1, g_issue, nm, lc, u, v);
-        g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+        ring_issue(ring, m + kRing - 1, walk.g, nm, lc, u, v);
+        walk.next(nn);
         pol.issue(m + kRing - 1);
     }
     cp_async_commit();
     cp_async_wait<kRing - 1>();  // the group holding row m is complete
     Slice<T> cur;
-    ring_read(ring, m, cur);
+    ring_read_bc<T, BC>(ring, m, rev, cur);
     pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
@@ -111,15 +165,16 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<T> (&W)[3]
 }
 
 // Geometry of one (band, strip) work item for depth K and halo H.
-// Input-row index q in 0 .. nout + 2K - 1 is global row r0 - K + q (wrapped);
-// the strip owns rows q in [K, K + nout) and lanes H .. 31-H whose column
-// sc = c0 + (lane - H) V is below NM.
+// Input-row index q in 0 .. nout + 2K - 1 is global row r0 - K + q (wrapped,
+// or reflected under zero flux); the strip owns rows q in [K, K + nout) and
+// lanes H .. 31-H whose column sc = c0 + (lane - H) V is below NM.  lc is the
+// first column the lane loads; rev marks a mirrored (reversed) vector.
 struct StripGeom {
     int lc, sc, r0, nout, total;
-    bool st_lane;
+    bool st_lane, rev;
 };
 
-template <typename T, int K, int H>
+template <typename T, int K, int H, int BC = BC_WRAP>
 __device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int nm, int rows) {
     constexpr int V = Vec<T>::N;
     static_assert(H * V >= K, "halo narrower than the temporal depth");
@@ -128,7 +183,17 @@ __device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int
     const int lane = threadIdx.x & 31;
     StripGeom g;
     const int c0 = band * OUTW;
-    g.lc = wrap_row((int64_t)c0 - H * V + lane * V, nm);  // V-aligned since nm % V == 0
+    const int64_t c = (int64_t)c0 - H * V + lane * V;
+    g.rev = false;
+    if constexpr (BC == BC_MIRROR) {
+        // columns c .. c+V-1 of the 2NM-periodic mirror image: inside the
+        // grid, or the reversed vector starting at 2NM - V - q (V-aligned)
+        const int q = wrap_row(c, 2 * (int64_t)nm);
+        g.rev = q >= nm;
+        g.lc = g.rev ? 2 * nm - V - q : q;
+    } else {
+        g.lc = wrap_row(c, nm);  // V-aligned since nm % V == 0
+    }
     g.sc = c0 + (lane - H) * V;
     g.st_lane = (lane >= H) && (lane < 32 - H) && (g.sc < nm);
     g.r0 = strip * rows;
@@ -139,7 +204,7 @@ __device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int
 
 // Run one work item through the K-stage pipeline: input rows of (u, v) pass
 // through the stages; the policy decides what each stage computes and stores.
-template <typename T, int K, class P>
+template <typename T, int K, int BC = BC_WRAP, class P>
 __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__restrict__ u,
                                                const T *__restrict__ v, int nn, int nm, P &pol) {
     Slice<T> W[3][K];
@@ -154,20 +219,21 @@ __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__
     ring.slot = ring_mem[(threadIdx.x >> 5) % kTemporalWarps];
 
     // prologue: rows 0 .. kRing-2 in flight, one commit group each
-    int g_issue = wrap_row((int64_t)geo.r0 - K, nn);
+    RowWalk<BC> walk;
+    walk.start((int64_t)geo.r0 - K, nn);
 #pragma unroll
     for (int j = 0; j < kRing - 1; ++j) {
         if (j < geo.total) {
-            ring_issue(ring, j, g_issue, nm, geo.lc, u, v);
-            g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+            ring_issue(ring, j, walk.g, nm, geo.lc, u, v);
+            walk.next(nn);
             pol.issue(j);
         }
         cp_async_commit();
     }
     for (int m = 0; m < geo.total; m += 3) {
-        pipeline_beat<T, K, 0>(m, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
-        pipeline_beat<T, K, 1>(m + 1, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
-        pipeline_beat<T, K, 2>(m + 2, geo.total, W, ring, g_issue, nn, nm, geo.lc, u, v, pol);
+        pipeline_beat<T, K, 0>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+        pipeline_beat<T, K, 1>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+        pipeline_beat<T, K, 2>(m + 2, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
     }
     cp_async_wait<0>();
 }
@@ -229,28 +295,28 @@ struct ForwardAllPolicy {
 // H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
 // needed only narrows the band), which lets a batched launch use one band
 // layout for launches of different depth.
-template <typename T, int K, int H, int RX>
+template <typename T, int K, int H, int RX, int BC = BC_WRAP>
 __device__ __forceinline__ void temporal_strip(int band, int strip, const T *__restrict__ u,
                                                const T *__restrict__ v, T *__restrict__ un,
                                                T *__restrict__ vn, int nn, int nm, int rows,
                                                const Coef<T> &p) {
-    const StripGeom geo = strip_geom<T, K, H>(band, strip, nn, nm, rows);
+    const StripGeom geo = strip_geom<T, K, H, BC>(band, strip, nn, nm, rows);
     ForwardPolicy<T, K, RX> pol{p, geo, un, vn, nm};
-    pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
+    pipeline_strip<T, K, BC>(geo, u, v, nn, nm, pol);
 }
 
 constexpr int kTemporalBlock = 32 * kTemporalWarps;
 
 // The single-grid temporally blocked kernel: warp w of the launch owns work
 // item (band w % bands, strip w / bands).
-template <typename T, int K, int RX>
+template <typename T, int K, int RX, int BC>
 __global__ void __launch_bounds__(kTemporalBlock)
 k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
            T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
     const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;  // whole warps only
     constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
-    temporal_strip<T, K, H, RX>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
+    temporal_strip<T, K, H, RX, BC>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
 }
 
 }  // namespace rdk

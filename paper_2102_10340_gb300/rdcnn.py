@@ -5,7 +5,11 @@ this module only allocates torch tensors, passes their pointers and the
 current CUDA stream, and turns status codes into exceptions.
 
 Model: Eq. 1-3 of Sec. II.A (FitzHugh-Nagumo reaction-diffusion CNN on a
-torus), gene {dt, a, b, eps, c, Du, Dv} with the paper's defaults.
+torus), gene {dt, a, b, eps, c, Du, Dv} with the paper's defaults.  Grids
+also take ``boundary="zeroflux"`` (ghost cell = edge cell) and
+``reaction="cenn"`` (Chua-Yang cell: u = state, v = constant offset plane,
+c = feedback centre, Du = feedback arms), the model variants the paper
+leaves to the user of its template (Sec. I, Sec. II.A).
 """
 from __future__ import annotations
 
@@ -21,7 +25,8 @@ GRAD_NAMES = ("Du", "Dv", "a", "b", "eps", "c")
 
 _VARIANTS = {"auto": L.VARIANT_AUTO, "step1": L.VARIANT_STEP1, "temporal": L.VARIANT_TEMPORAL,
              "generic": L.VARIANT_GENERIC, "temporal2": L.VARIANT_TEMPORAL2}
-_REACTIONS = {"fhn": L.REACTION_FHN, "none": L.REACTION_NONE}
+_REACTIONS = {"fhn": L.REACTION_FHN, "none": L.REACTION_NONE, "cenn": L.REACTION_CENN}
+_BOUNDARIES = {"periodic": L.BC_PERIODIC, "zeroflux": L.BC_ZEROFLUX}
 
 
 def _dtype_code(dtype: torch.dtype) -> int:
@@ -74,17 +79,18 @@ class Grid:
     """
 
     def __init__(self, nn: int, nm: int, params: dict | None = None, dtype=torch.float32,
-                 reaction: str = "fhn", device="cuda"):
+                 reaction: str = "fhn", device="cuda", boundary: str = "periodic"):
         self.lib = L.load()
         self.nn, self.nm = int(nn), int(nm)
         self.dtype = dtype
         self.device = torch.device(device)
         self.params = _params(params)
         self.reaction = reaction
+        self.boundary = boundary
         h = ctypes.c_void_p()
         ps = L.params_struct(self.params)
-        rc = self.lib.rdcnn_create(ctypes.byref(h), self.nn, self.nm, ctypes.byref(ps), L.BC_PERIODIC,
-                                   _dtype_code(dtype), _REACTIONS[reaction])
+        rc = self.lib.rdcnn_create(ctypes.byref(h), self.nn, self.nm, ctypes.byref(ps),
+                                   _BOUNDARIES[boundary], _dtype_code(dtype), _REACTIONS[reaction])
         L.check(rc)
         _warn(rc)
         self.h = h
@@ -150,6 +156,16 @@ class Grid:
         self._bind()
         L.check(self.lib.rdcnn_run(self.h, int(T), _VARIANTS[variant], int(k)))
         return self
+
+    def plan(self, variant: str = "auto", k: int = 0) -> dict:
+        """The launch shape run(T, variant, k) uses: {"variant", "k", "rows"} with AUTO, the
+        default depth and the launcher's own rows choice resolved (nothing runs)."""
+        var = ctypes.c_int(_VARIANTS[variant])
+        tune = L.Tune(int(k), 0)
+        self._bind()
+        L.check(self.lib.rdcnn_plan(self.h, ctypes.byref(var), ctypes.byref(tune)))
+        name = {code: n for n, code in _VARIANTS.items()}[var.value]
+        return {"variant": name, "k": tune.k, "rows": tune.rows}
 
     def run_snapshots(self, T: int, every: int, out: str = "host", n_stage: int = 2, pin: bool = True,
                       buffers=None):
@@ -242,7 +258,7 @@ class Grid:
 
 
 def run(u: torch.Tensor, v: torch.Tensor, params: dict | None, T: int, variant: str = "auto",
-        k: int = 0, reaction: str = "fhn"):
+        k: int = 0, reaction: str = "fhn", boundary: str = "periodic"):
     """Advance (u, v) in place by T steps of Eq. 1 (scratch allocated by torch)."""
     if u.shape != v.shape or u.dim() != 2:
         raise ValueError("u and v must be 2-D planes of the same shape")
@@ -252,7 +268,7 @@ def run(u: torch.Tensor, v: torch.Tensor, params: dict | None, T: int, variant: 
     _plane_check(v, nn, nm, u.dtype, "v")
     h = ctypes.c_void_p()
     ps = L.params_struct(_params(params))
-    rc = L.check(lib.rdcnn_create(ctypes.byref(h), nn, nm, ctypes.byref(ps), L.BC_PERIODIC,
+    rc = L.check(lib.rdcnn_create(ctypes.byref(h), nn, nm, ctypes.byref(ps), _BOUNDARIES[boundary],
                                   _dtype_code(u.dtype), _REACTIONS[reaction]))
     _warn(rc)
     try:

@@ -16,12 +16,13 @@ def cpu_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
-def gpu_run(rd, u0, v0, params, T, dtype, variant="auto", k=0, reaction="fhn", rows=0):
+def gpu_run(rd, u0, v0, params, T, dtype, variant="auto", k=0, reaction="fhn", rows=0,
+            boundary="periodic"):
     """Run T steps on the GPU through the C ABI; returns float64 numpy (u_T, v_T)."""
     import torch
 
     u0 = np.asarray(u0)
-    g = rd.Grid(u0.shape[0], u0.shape[1], params, dtype=dtype, reaction=reaction)
+    g = rd.Grid(u0.shape[0], u0.shape[1], params, dtype=dtype, reaction=reaction, boundary=boundary)
     if rows:
         g.set_tune(k=k, rows=rows)
     g.set_state(torch.from_numpy(np.ascontiguousarray(u0)).to("cuda", dtype),

@@ -72,7 +72,7 @@ def _create(lib, L, nn=8, nm=8, params=None, boundary=0, dtype=0, reaction=0):
 def test_create_validation(lib, L):
     assert _create(lib, L, nn=0)[0] == L.EINVAL
     assert _create(lib, L, nm=-3)[0] == L.EINVAL
-    assert _create(lib, L, boundary=1)[0] == L.EINVAL
+    assert _create(lib, L, boundary=2)[0] == L.EINVAL
     assert _create(lib, L, dtype=7)[0] == L.EINVAL
     assert _create(lib, L, reaction=5)[0] == L.EINVAL
     bad = {"dt": 0.1, "a": math.nan, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0}
@@ -158,3 +158,61 @@ def test_adjoint_validation(lib, L):
 def test_version_and_counter(lib):
     assert b"rdcnn" in lib.rdcnn_version()
     assert lib.rdcnn_launch_count() >= 0
+
+
+def header_enums():
+    """Every RDCNN_* enumerator of the header with its value."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"RDCNN_(\w+)\s*=\s*(-?\d+)", body):
+            out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_header(L):
+    enums = header_enums()
+    for name in ("BC_PERIODIC", "BC_ZEROFLUX", "F32", "F64", "REACTION_FHN", "REACTION_NONE",
+                 "REACTION_CENN", "VARIANT_AUTO", "VARIANT_STEP1", "VARIANT_TEMPORAL",
+                 "VARIANT_GENERIC", "VARIANT_TEMPORAL2"):
+        assert getattr(L, name) == enums[name], name
+
+
+def test_create_accepts_models_and_rejects_bad_enums(lib, L):
+    p = L.params_struct({"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0})
+    for bc in (L.BC_PERIODIC, L.BC_ZEROFLUX):
+        for rx in (L.REACTION_FHN, L.REACTION_NONE, L.REACTION_CENN):
+            h = ctypes.c_void_p()
+            assert lib.rdcnn_create(ctypes.byref(h), 8, 8, ctypes.byref(p), bc, L.F32, rx) == 0
+            lib.rdcnn_destroy(h)
+    h = ctypes.c_void_p()
+    assert lib.rdcnn_create(ctypes.byref(h), 8, 8, ctypes.byref(p), 2, L.F32, L.REACTION_FHN) == L.EINVAL
+    assert lib.rdcnn_create(ctypes.byref(h), 8, 8, ctypes.byref(p), L.BC_PERIODIC, L.F32, 3) == L.EINVAL
+    # CeNN feedback arms may be negative; diffusion coefficients may not
+    q = L.params_struct({"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 2.0, "Du": -0.5, "Dv": 0.0})
+    assert lib.rdcnn_create(ctypes.byref(h), 8, 8, ctypes.byref(q), L.BC_ZEROFLUX, L.F32, L.REACTION_CENN) == 0
+    lib.rdcnn_destroy(h)
+    assert lib.rdcnn_create(ctypes.byref(h), 8, 8, ctypes.byref(q), L.BC_ZEROFLUX, L.F32, L.REACTION_FHN) == L.EINVAL
+
+
+def test_plan_resolves_without_running(lib, L):
+    """rdcnn_plan for the variants whose shape needs no device query (no CUDA work)."""
+    h = _create(lib, L, nn=64, nm=64)[1]
+    var = ctypes.c_int(L.VARIANT_STEP1)
+    tune = L.Tune(0, 0)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == 0
+    assert (var.value, tune.k, tune.rows) == (L.VARIANT_STEP1, 1, 4)
+    assert lib.rdcnn_set_tune(h, ctypes.byref(L.Tune(0, 16))) == 0
+    tune = L.Tune(0, 0)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == 0 and tune.rows == 16
+    var = ctypes.c_int(L.VARIANT_GENERIC)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == 0 and (tune.k, tune.rows) == (1, 0)
+    var = ctypes.c_int(L.VARIANT_TEMPORAL)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(L.Tune(9, 0))) == L.EINVAL  # k > 8
+    var = ctypes.c_int(17)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == L.EINVAL
+    lib.rdcnn_destroy(h)
+    h = _create(lib, L, nn=64, nm=64, boundary=L.BC_ZEROFLUX)[1]
+    var = ctypes.c_int(L.VARIANT_TEMPORAL2)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(L.Tune(4, 0))) == L.EINVAL
+    lib.rdcnn_destroy(h)
