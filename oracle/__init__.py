@@ -19,6 +19,10 @@ Functions and the passages they follow:
   feedback centre c, arms Du, offset plane w held in v).  Sec. I and II.A
   present the framework as a template for such models without fixing one;
   both are readings, written out in ``rdcnn_oracle.c``.
+* :func:`run_storage`, :func:`step_f32`, :func:`round_to_storage` -- the
+  reduced-precision storage variant (16-bit planes, FP32 arithmetic, the
+  state rounded to the storage format after every k-step block); not in the
+  paper, the arithmetic is Eq. 1-3 in FP32 in their literal order.
 * :func:`scalar_map` -- Eq. 1 for an isolated cell (no diffusion term).
 * :func:`adjoint` -- exact discrete adjoint of Eq. 1-3 (not in the paper;
   derivation in ``rdcnn_oracle.c``).
@@ -201,6 +205,16 @@ class Oracle:
     def summary(self, u, v, threshold: float, precision=np.float64):
         return summary(u, v, threshold, precision)
 
+    def round_to_storage(self, x, storage: str):
+        return round_to_storage(x, storage)
+
+    def step_f32(self, u, v, params: dict, reaction: int = FHN, boundary: int = PERIODIC):
+        return step_f32(u, v, params, reaction, boundary)
+
+    def run_storage(self, u, v, params: dict, T: int, k: int, storage: str, reaction: int = FHN,
+                    boundary: int = PERIODIC):
+        return run_storage(u, v, params, T, k, storage, reaction, boundary)
+
 
 def _get() -> Oracle:
     global _default
@@ -271,6 +285,83 @@ def run_numpy(u, v, params: dict, T: int, reaction: int = FHN, boundary: int = P
     for _ in range(int(T)):
         u, v = step_numpy(u, v, params, reaction, boundary)
     return _plane(u), _plane(v)
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision storage: the state planes are held in a 16-bit format,
+# the arithmetic is FP32, and the state is rounded to the storage format at
+# the end of every block of k steps (one HBM round trip of a k-step launch).
+# Not in the paper (its listings use float32 throughout); the rounding is a
+# quantisation, so it is decided on FP32 values as the kernels decide it.
+# ---------------------------------------------------------------------------
+
+STORAGE_FORMATS = ("f32", "f16", "bf16")
+
+
+def round_to_storage(x, storage: str) -> np.ndarray:
+    """Round FP32 values to the storage format (nearest, ties to even); returns float32.
+
+    bf16 = the upper 16 bits of an IEEE single (8 exponent bits, 7 fraction bits): add
+    0x7FFF plus the lowest kept bit to the 32-bit pattern and clear the low 16 bits.
+    f16 = IEEE half (numpy's conversion).  Finite inputs within range only."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if storage == "f32":
+        return x.copy()
+    if storage == "f16":
+        return x.astype(np.float16).astype(np.float32)
+    if storage == "bf16":
+        bits = x.view(np.uint32).astype(np.uint64)
+        keep_lsb = (bits >> 16) & 1
+        rounded = ((bits + 0x7FFF + keep_lsb) & 0xFFFF0000).astype(np.uint32)
+        return rounded.view(np.float32)
+    raise ValueError(f"storage must be one of {STORAGE_FORMATS}")
+
+
+def step_f32(u, v, params: dict, reaction: int = FHN, boundary: int = PERIODIC):
+    """One application of the update in FP32 (numpy float32 arrays: every operation rounded
+    to single precision as written, no fused multiply-add), in the literal form of Eq. 1-3:
+    neighbour sum ((n + s) + (w + e)) - 4 centre, f1 = c u - u^3/3 - v, f2 = -eps (u - b v + a);
+    the CeNN cell as in step_numpy."""
+    u = np.asarray(u, dtype=np.float32)
+    v = np.asarray(v, dtype=np.float32)
+    dt, a, b, eps, c, Du, Dv = (np.float32(x) for x in pvec(params))
+    four, three = np.float32(4.0), np.float32(3.0)
+    if reaction == CENN:
+        y = np.clip(u, np.float32(-1.0), np.float32(1.0))
+        n, s_, w, e = _neighbours(y, boundary)
+        feedback = c * y + Du * ((n + s_) + (w + e))
+        return u + dt * ((-u + feedback) + v), v.copy()
+
+    def lap(f):
+        n, s_, w, e = _neighbours(f, boundary)
+        return ((n + s_) + (w + e)) - four * f
+
+    if reaction == FHN:
+        f1 = c * u - (u * u * u) / three - v
+        f2 = -eps * (u - b * v + a)
+    else:
+        f1 = np.zeros_like(u)
+        f2 = np.zeros_like(v)
+    return u + dt * (f1 + Du * lap(u)), v + dt * (f2 + Dv * lap(v))
+
+
+def run_storage(u, v, params: dict, T: int, k: int, storage: str, reaction: int = FHN,
+                boundary: int = PERIODIC):
+    """T steps with the state stored in `storage`: the start state is rounded to the format,
+    then each block of k steps (the last block may be shorter) runs in FP32 and ends with
+    both planes rounded to the format.  Returns float32 arrays."""
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    u = round_to_storage(u, storage)
+    v = round_to_storage(v, storage)
+    left = int(T)
+    while left > 0:
+        kk = min(k, left)
+        for _ in range(kk):
+            u, v = step_f32(u, v, params, reaction, boundary)
+        u, v = round_to_storage(u, storage), round_to_storage(v, storage)
+        left -= kk
+    return u, v
 
 
 # ---------------------------------------------------------------------------

@@ -481,3 +481,84 @@ def test_cenn_numpy_formulation_agrees(oracle_mod):
         n = oracle_mod.run_numpy(x, w, g, 25, reaction=oracle_mod.CENN, boundary=b)
         np.testing.assert_allclose(a[0], n[0], rtol=0, atol=1e-12)
         assert np.array_equal(a[1], w)
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision storage (16-bit planes, FP32 arithmetic, rounding after
+# every k-step block).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage,cases", [
+    ("bf16", [(1.0, 1.0), (1 + 2**-8, 1.0), (1 + 3 * 2**-8, 1 + 2**-6), (1 + 2**-8 + 2**-20, 1 + 2**-7),
+              (-(1 + 2**-8 + 2**-20), -(1 + 2**-7)), (3.0, 3.0), (0.1, 0.10009765625), (2.0**-130, 2.0**-130)]),
+    ("f16", [(1.0, 1.0), (1 + 2**-11, 1.0), (1 + 3 * 2**-11, 1 + 2**-9), (65504.0, 65504.0),
+             (2.0**-24, 2.0**-24), (0.1, 0.0999755859375), (-0.1, -0.0999755859375)]),
+])
+def test_round_to_storage_known_values(oracle_mod, storage, cases):
+    """Nearest representable value, ties to the even significand (values worked by hand)."""
+    got = oracle_mod.round_to_storage(np.array([c[0] for c in cases], dtype=np.float32), storage)
+    np.testing.assert_array_equal(got, np.array([c[1] for c in cases], dtype=np.float32))
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_round_to_storage_matches_torch_conversion(oracle_mod, storage):
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(11).uniform(-5, 5, 20000).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16 if storage == "bf16" else torch.float16).float().numpy()
+    np.testing.assert_array_equal(oracle_mod.round_to_storage(x, storage), ref)
+
+
+@pytest.mark.parametrize("reaction,boundary", [("FHN", "PERIODIC"), ("NONE", "ZEROFLUX"), ("CENN", "ZEROFLUX")])
+def test_step_f32_is_one_rounded_step(oracle_mod, reaction, boundary):
+    """The FP32 step stays within a few single-precision rounding units of the FP64 step."""
+    rx, bc = getattr(oracle_mod, reaction), getattr(oracle_mod, boundary)
+    gene = CENN_GENE if reaction == "CENN" else ODD_GENE
+    x = (1.5 * inp.uniform_field(80, 13, 21)).astype(np.float32).astype(np.float64)
+    y = (0.4 * inp.uniform_field(81, 13, 21)).astype(np.float32).astype(np.float64)
+    u32, v32 = oracle_mod.step_f32(x, y, gene, rx, bc)
+    u64, v64 = oracle_mod.step(x, y, gene, rx, boundary=bc)
+    assert u32.dtype == np.float32
+    scale = max(np.abs(u64).max(), np.abs(v64).max())
+    assert np.abs(u32 - u64).max() <= 1e-6 * scale and np.abs(v32 - v64).max() <= 1e-6 * scale
+
+
+def test_run_storage_f32_follows_fp64(oracle_mod):
+    x = inp.uniform_field(82, 32, 40)
+    u, v = oracle_mod.run_storage(x, x, inp.default_params(), 60, 7, "f32")
+    ru, rv = oracle_mod.run(x.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64),
+                            inp.default_params(), 60)
+    assert np.linalg.norm(u - ru) / np.linalg.norm(ru) < 1e-5
+    assert np.linalg.norm(v - rv) / np.linalg.norm(rv) < 1e-5
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_run_storage_returns_representable_values(oracle_mod, storage):
+    x = inp.uniform_field(83, 24, 24)
+    u, v = oracle_mod.run_storage(x, 0.5 * x, inp.default_params(), 30, 4, storage)
+    assert np.array_equal(oracle_mod.round_to_storage(u, storage), u)
+    assert np.array_equal(oracle_mod.round_to_storage(v, storage), v)
+
+
+def test_bf16_storage_freezes_sub_half_ulp_increments(oracle_mod):
+    """Pure diffusion of one bump of one bf16 unit (2^-7) on a field of ones, dt Du = 0.006:
+    rounded every step (k = 1) the bump keeps its value (its loss, 0.024 units, is below half a
+    unit) and every neighbour's gain (0.006 units) rounds away, so the state never changes;
+    rounded once after 50 steps, the FP32 increments accumulate and the bump decays."""
+    u = np.ones((9, 9))
+    u[4, 4] = 1 + 2**-7
+    par = inp.default_params()
+    uk1, _ = oracle_mod.run_storage(u, u, par, 50, 1, "bf16", reaction=oracle_mod.NONE)
+    assert np.array_equal(uk1, u.astype(np.float32))
+    uk50, _ = oracle_mod.run_storage(u, u, par, 50, 50, "bf16", reaction=oracle_mod.NONE)
+    assert uk50[4, 4] == 1.0 and not np.array_equal(uk50, u.astype(np.float32))
+
+
+def test_fewer_roundings_mean_smaller_storage_error(oracle_mod):
+    x = inp.uniform_field(84, 48, 48)
+    ref, _ = oracle_mod.run(x.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64),
+                            inp.default_params(), 96)
+    err = {}
+    for k in (1, 8, 96):
+        u, _ = oracle_mod.run_storage(x, x, inp.default_params(), 96, k, "bf16")
+        err[k] = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    assert err[96] < err[8] < err[1]
