@@ -281,6 +281,64 @@ def measure_models(rd, torch, N=N_GRID, quick=False):
             "note": "per-launch CUDA-event time; fhn_periodic is the paper's model for comparison"}
 
 
+def measure_storage(rd, torch, N=N_GRID, quick=False):
+    """Throughput of 16-bit state storage (FP32 arithmetic) against FP32 storage on the headline
+    grid: the single-step kernel (HBM-bound: 8 instead of 16 algorithmic bytes per cell-step)
+    and the temporal kernel (k = 8, 128 rows), per launch, CUDA events on the launching stream."""
+    if quick:
+        N = 1024
+    x = torch.from_numpy(np.asarray(inp.mid_patch(0, N, N), dtype=np.float32)).cuda()
+    peaks = load_peaks()
+    out = {}
+    for name, dt, esz in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
+        g = rd.Grid(N, N, inp.default_params(), dtype=dt)
+        g.set_state(x.to(dt), x.to(dt))
+        res = {}
+        for variant, k, rows in (("temporal", 8, 128), ("step1", 1, 0)):
+            g.set_tune(k=k, rows=rows)
+            ms = measure_launch_ms(rd, g, variant, k, 4, 10, torch)
+            res[variant] = {"k": k, "launch_ms": ms, "gcell_s": N * N * k / (ms * 1e-3) / 1e9}
+        gbs = 4 * esz * N * N / (res["step1"]["launch_ms"] * 1e-3) / 1e9
+        res["step1"].update({"algorithmic_bytes_per_cell_step": 4 * esz, "achieved_gbs": gbs,
+                             "frac_hbm": gbs / peaks["hbm_gbs"]})
+        out[name] = res
+        g.close()
+    return {"grid": [N, N], "storage": out, "error": measure_storage_error(rd, torch, quick=quick),
+            "note": "16-bit planes hold the state; every launch computes in FP32 and rounds once on store"}
+
+
+def measure_storage_error(rd, torch, N=512, quick=False):
+    """Accuracy cost of 16-bit storage: normwise distance of u_T (and of the gradient-area
+    statistic) from the FP64 kernels' u_T (pinned to the oracle at 1e-12) on an N x N grid,
+    default gene, x ~ U[-1, 1] seed 0, u = v = x, for storage formats and steps per launch."""
+    x = np.asarray(inp.uniform_field(0, N, N), dtype=np.float32)
+    xt = torch.from_numpy(x).cuda()
+    Ts = (100, 1000) if quick else (100, 1000, 5000)
+
+    def run(dt, variant, k, T):
+        g = rd.Grid(N, N, inp.default_params(), dtype=dt)
+        g.set_state(xt.to(dt), xt.to(dt))
+        g.run(T, variant=variant, k=k)
+        u, v = g.state()
+        g.close()
+        return u.double(), v.double()
+
+    out = {}
+    for T in Ts:
+        ru, rv = run(torch.float64, "temporal", 4, T)
+        ref_edge = float(rd.grid_summary(ru, rv)[rd.SUMMARY_FIELDS.index("edge_frac")])
+        row = {}
+        for name, dt, variant, k in (("f32_k8", torch.float32, "temporal", 8), ("bf16_k1", torch.bfloat16, "step1", 1),
+                                     ("bf16_k8", torch.bfloat16, "temporal", 8), ("f16_k1", torch.float16, "step1", 1),
+                                     ("f16_k8", torch.float16, "temporal", 8)):
+            u, v = run(dt, variant, k, T)
+            edge = float(rd.grid_summary(u, v)[rd.SUMMARY_FIELDS.index("edge_frac")])
+            row[name] = {"normwise_u": float(torch.linalg.norm(u - ru) / torch.linalg.norm(ru)),
+                         "edge_frac": edge, "edge_frac_ref": ref_edge}
+        out[f"T={T}"] = row
+    return {"grid": [N, N], "init": "x ~ U[-1,1] seed 0, u = v = x", "reference": "FP64 kernels", "runs": out}
+
+
 def measure_batched(rd, torch, T=5000, quick=False):
     specs = inp.sweep_instances(0)
     if quick:
@@ -521,6 +579,7 @@ def run_ours(args):
         extra["search"] = measure_search(torch, quick=args.quick)
         extra["adjoint"] = measure_adjoint(rd, torch, quick=args.quick)
         extra["models"] = measure_models(rd, torch, quick=args.quick)
+        extra["storage"] = measure_storage(rd, torch, quick=args.quick)
     cpu = None if args.no_cpu else oracle_sample(6.0 if args.quick else 12.0, n=N)
 
     line = {"metric": METRIC, "value": value, "unit": "Gcell-updates/s", "n_gpus": world,
@@ -553,7 +612,7 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
-    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models"), default=None,
+    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage"), default=None,
                     help="run only this follow-on measurement (small, for profiling) and print it")
     ap.add_argument("--variant", default="temporal", choices=("temporal", "temporal2", "step1", "generic"))
     ap.add_argument("--k", type=int, default=8)
@@ -571,7 +630,8 @@ def main(argv=None):
         fn = {"batched": lambda: measure_batched(rd, torch, quick=True),
               "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
               "search": lambda: measure_search(torch, quick=True),
-              "models": lambda: measure_models(rd, torch)}[args.leg]
+              "models": lambda: measure_models(rd, torch),
+              "storage": lambda: measure_storage(rd, torch)}[args.leg]
         print(json.dumps({"leg": args.leg, **fn()}), flush=True)
         return 0
     return run_ours(args)

@@ -27,6 +27,16 @@
  *      v+_ij = v_ij
  *    a, b, eps and Dv are ignored (they must still be finite).
  *
+ * Reduced-precision storage (not in the paper): a handle of dtype RDCNN_BF16
+ * or RDCNN_F16 keeps u, v and the workspace in 16-bit planes (bfloat16 /
+ * IEEE half, element type uint16_t-sized) and computes every step in FP32;
+ * a launch loads 16-bit values, advances them its k steps in FP32 registers
+ * and rounds the result to nearest (ties to even) when it stores it.  This
+ * halves the bytes per cell-step of the single-step kernel (8 B instead of
+ * 16) at the cost of one 16-bit rounding per launch.  Supported by
+ * rdcnn_init / set_state / run / get_state / run_snapshots / plan; the
+ * batched, adjoint, static-scratch and TEMPORAL2 paths return RDCNN_EINVAL.
+ *
  * Conventions shared by every entry point
  *  - Layout: one plane per field, row-major [NN][NM], element (i, j) at
  *    offset i * NM + j; i is the row (NN rows), j the column (NM columns).
@@ -75,7 +85,9 @@ enum rdcnn_status {
 
 enum { RDCNN_BC_PERIODIC = 0,                    /* toroidal wrap, Sec. II.B-II.C */
        RDCNN_BC_ZEROFLUX = 1 };                   /* ghost cell = edge cell (see above) */
-enum { RDCNN_F32 = 0, RDCNN_F64 = 1 };
+enum { RDCNN_F32 = 0, RDCNN_F64 = 1,
+       RDCNN_BF16 = 2,                            /* bf16 planes, FP32 arithmetic (see below) */
+       RDCNN_F16 = 3 };                           /* IEEE half planes, FP32 arithmetic */
 enum { RDCNN_REACTION_FHN = 0,                    /* Eq. 2-3 */
        RDCNN_REACTION_NONE = 1,                   /* f1 = f2 = 0: pure diffusion (testing) */
        RDCNN_REACTION_CENN = 2 };                 /* Chua-Yang cell (see above) */
@@ -118,7 +130,8 @@ int rdcnn_set_params(rdcnn_t *h, const rdcnn_params *p);
 int rdcnn_set_tune(rdcnn_t *h, const rdcnn_tune *tune);
 
 /* Bytes of device scratch rdcnn_run needs: two planes (the "Anew"/"Bnew"
- * ping-pong partners of Sec. II.B), NN * NM * sizeof(element) each. */
+ * ping-pong partners of Sec. II.B) of NN * NM * sizeof(element) bytes each,
+ * the second starting at the first one's size rounded up to 256 bytes. */
 int rdcnn_workspace_bytes(const rdcnn_t *h, size_t *bytes);
 
 /* Attach caller-owned device buffers: u and v planes (the state, updated in
@@ -142,10 +155,14 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
 
 /* Apply Eq. 1 T times (t = 1..T, Sec. II.A) to the bound state, in place.
  * variant: RDCNN_VARIANT_*; k: time steps fused per launch for the temporal
- * variants (0 = library default; 1..8 for F32, 1..4 for F64).  All variants
- * give bit-identical results; they differ only in speed.  T = 0 is a
- * no-op.  Asynchronous on the bound stream.  The vectorised variants need
- * NM to be a multiple of 4 (F32) or 2 (F64) and 16-byte aligned buffers;
+ * variants (0 = library default; 1..8 for F32 / BF16 / F16, 1..4 for F64).
+ * For F32 and F64 all variants give bit-identical results; they differ only
+ * in speed.  For BF16 / F16 every launch rounds the state once when it
+ * stores it, so results depend on the steps per launch (k for TEMPORAL, 1
+ * for STEP1 and GENERIC); variants with the same k agree bit for bit.
+ * T = 0 is a no-op.  Asynchronous on the bound stream.  The vectorised
+ * variants need NM to be a multiple of 4 (F32, BF16, F16) or 2 (F64) and
+ * 16-byte (8-byte for BF16 / F16) aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns
  * RDCNN_EINVAL.  The handle's reaction and boundary apply to every variant
  * except RDCNN_VARIANT_TEMPORAL2, which returns RDCNN_EINVAL for ZEROFLUX

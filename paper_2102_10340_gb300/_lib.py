@@ -30,6 +30,8 @@ BC_PERIODIC = 0
 BC_ZEROFLUX = 1
 F32 = 0
 F64 = 1
+BF16 = 2
+F16 = 3
 REACTION_FHN = 0
 REACTION_NONE = 1
 REACTION_CENN = 2

@@ -438,6 +438,7 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
     const int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s);
     if (rc < 0) return rc;
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
+    if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
     *bytes = adj_layout(dtype, nn, nm, T, n_checkpoints).total;
     return RDCNN_OK;
 }
@@ -450,6 +451,7 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     if (rc < 0) return rc;
     if (boundary != RDCNN_BC_PERIODIC || reaction == RDCNN_REACTION_CENN)
         return set_error(RDCNN_EINVAL, "the adjoint supports the periodic FHN / NONE models only");
+    if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
         return set_error(RDCNN_EINVAL, "NULL argument");

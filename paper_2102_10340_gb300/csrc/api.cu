@@ -81,7 +81,8 @@ int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p, i
         return set_error(RDCNN_EINVAL, "grid too large");
     if (boundary != RDCNN_BC_PERIODIC && boundary != RDCNN_BC_ZEROFLUX)
         return set_error(RDCNN_EINVAL, "boundary must be RDCNN_BC_PERIODIC or RDCNN_BC_ZEROFLUX");
-    if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "dtype must be RDCNN_F32 or RDCNN_F64");
+    if (dtype != RDCNN_F32 && dtype != RDCNN_F64 && dtype != RDCNN_BF16 && dtype != RDCNN_F16)
+        return set_error(RDCNN_EINVAL, "dtype must be RDCNN_F32, RDCNN_F64, RDCNN_BF16 or RDCNN_F16");
     if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE && reaction != RDCNN_REACTION_CENN)
         return set_error(RDCNN_EINVAL, "unknown reaction");
     const int pc = check_params(p, reaction);
@@ -114,7 +115,8 @@ int rdcnn_set_tune(rdcnn_t *h, const rdcnn_tune *tune) {
 
 int rdcnn_workspace_bytes(const rdcnn_t *h, size_t *bytes) {
     if (!h || !bytes) return set_error(RDCNN_EINVAL, "NULL argument");
-    *bytes = 2 * (size_t)h->nn * (size_t)h->nm * elem_size(h->dtype);
+    const size_t plane = (size_t)h->nn * (size_t)h->nm * elem_size(h->dtype);
+    *bytes = plane_stride(plane) + plane;
     return RDCNN_OK;
 }
 
@@ -180,11 +182,12 @@ static int resolve_variant(const rdcnn_t *h, bool vec_ok, int *variant, int *k) 
     if ((*variant == RDCNN_VARIANT_STEP1 || *variant == RDCNN_VARIANT_TEMPORAL ||
          *variant == RDCNN_VARIANT_TEMPORAL2) && !vec_ok)
         return set_error(RDCNN_EINVAL,
-                         "vectorised variants need NM %% %d == 0 and 16-byte aligned buffers",
-                         vec_width(h->dtype));
+                         "vectorised variants need NM %% %d == 0 and %d-byte aligned buffers",
+                         vec_width(h->dtype), (int)vec_align(h->dtype));
     if (*variant == RDCNN_VARIANT_TEMPORAL2 &&
-        (h->boundary != RDCNN_BC_PERIODIC || h->reaction == RDCNN_REACTION_CENN))
-        return set_error(RDCNN_EINVAL, "RDCNN_VARIANT_TEMPORAL2 supports the periodic FHN / NONE models only");
+        (h->boundary != RDCNN_BC_PERIODIC || h->reaction == RDCNN_REACTION_CENN || is_16bit(h->dtype)))
+        return set_error(RDCNN_EINVAL,
+                         "RDCNN_VARIANT_TEMPORAL2 supports the periodic FHN / NONE models in FP32 / FP64 only");
     if (*variant == RDCNN_VARIANT_TEMPORAL || *variant == RDCNN_VARIANT_TEMPORAL2) {
         if (*k == 0) *k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
         if (*k < 1 || *k > max_k(h->dtype))
@@ -200,7 +203,9 @@ static bool vec_ok_for(const rdcnn_t *h) {
     if (!h->bound) return nm_ok;
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
     const char *ws = (const char *)h->ws;
-    return nm_ok && aligned16(h->u) && aligned16(h->v) && aligned16(ws) && aligned16(ws + plane);
+    const size_t a = vec_align(h->dtype);
+    return nm_ok && aligned_to(h->u, a) && aligned_to(h->v, a) && aligned_to(ws, a) &&
+           aligned_to(ws + plane_stride(plane), a);
 }
 
 int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx) {
@@ -212,7 +217,7 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
     if (T == 0) return RDCNN_OK;
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
     char *ws = (char *)h->ws;
-    void *su = ws, *sv = ws + plane;
+    void *su = ws, *sv = ws + plane_stride(plane);
     const int rv = resolve_variant(h, vec_ok_for(h), &variant, &k);
     if (rv < 0) return rv;
     const void *cu = h->u, *cv = h->v;

@@ -12,6 +12,8 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "rdcnn.h"
@@ -46,16 +48,127 @@ inline cudaError_t with_model(int reaction, int boundary, F &&f) {
     }
 }
 
-// 16-byte vector of the element type: the unit each lane loads and stores.
-template <typename T> struct Vec;
-template <> struct Vec<float> {
-    typedef float4 type;
-    static constexpr int N = 4;
+// Host-side dispatch of a storage dtype (RDCNN_F32 / F64 / BF16 / F16) to a
+// callable taking a value of that type as a tag, and of a temporal depth
+// 1..8 to a callable taking IntC<K>.
+template <class F>
+inline auto with_dtype(int dtype, F &&f) {
+    switch (dtype) {
+        case RDCNN_F64: return f(double{});
+        case RDCNN_BF16: return f(__nv_bfloat16{});
+        case RDCNN_F16: return f(__half{});
+        default: return f(float{});
+    }
+}
+template <class F>
+inline cudaError_t with_depth(int k, F &&f) {
+    switch (k) {
+        case 1: return f(IntC<1>{});
+        case 2: return f(IntC<2>{});
+        case 3: return f(IntC<3>{});
+        case 4: return f(IntC<4>{});
+        case 5: return f(IntC<5>{});
+        case 6: return f(IntC<6>{});
+        case 7: return f(IntC<7>{});
+        case 8: return f(IntC<8>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+// Deepest temporal pipeline per storage type (register budget).
+template <typename T> struct MaxDepth : IntC<8> {};
+template <> struct MaxDepth<double> : IntC<4> {};
+
+// V values of storage type T held by one lane: 16 bytes (float x 4,
+// double x 2) or 8 bytes (16-bit x 4).
+template <typename T, int V> struct LaneVec;
+template <> struct LaneVec<float, 4> { typedef float4 type; };
+template <> struct LaneVec<double, 2> { typedef double2 type; };
+template <> struct LaneVec<__nv_bfloat16, 4> { typedef uint2 type; };
+template <> struct LaneVec<__half, 4> { typedef uint2 type; };
+
+// Lane width of the register pipelines: 4 values (2 doubles) of every
+// storage type, so that 16-bit planes share the FP32 lane layout and
+// register budget (8 bytes per lane and field).
+template <typename T> struct Vec {
+    static constexpr int N = std::is_same<T, double>::value ? 2 : 4;
+    typedef typename LaneVec<T, N>::type type;
 };
-template <> struct Vec<double> {
-    typedef double2 type;
-    static constexpr int N = 2;
-};
+
+// Arithmetic type of a storage type: 16-bit planes are computed in FP32 and
+// rounded (to nearest, ties to even) only when stored.
+template <typename T> struct Compute { typedef T type; };
+template <> struct Compute<__nv_bfloat16> { typedef float type; };
+template <> struct Compute<__half> { typedef float type; };
+template <typename T> using CT = typename Compute<T>::type;
+
+template <typename T>
+constexpr bool is_wide() { return std::is_same<T, float>::value || std::is_same<T, double>::value; }
+
+// Storage vector <-> compute values.
+template <typename T, int V>
+__device__ __forceinline__ void unpack_vec(const typename LaneVec<T, V>::type &x, CT<T> (&d)[V]) {
+    if constexpr (std::is_same<T, float>::value) {
+        d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+    } else if constexpr (std::is_same<T, double>::value) {
+        d[0] = x.x; d[1] = x.y;
+    } else {
+        const unsigned *w = reinterpret_cast<const unsigned *>(&x);  // two values per word
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            float2 f;
+            if constexpr (std::is_same<T, __nv_bfloat16>::value)
+                f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[i]));
+            else
+                f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+            d[2 * i] = f.x;
+            d[2 * i + 1] = f.y;
+        }
+    }
+}
+template <typename T, int V>
+__device__ __forceinline__ typename LaneVec<T, V>::type pack_vec(const CT<T> (&s)[V]) {
+    if constexpr (std::is_same<T, float>::value) {
+        return make_float4(s[0], s[1], s[2], s[3]);
+    } else if constexpr (std::is_same<T, double>::value) {
+        return make_double2(s[0], s[1]);
+    } else {
+        typename LaneVec<T, V>::type r;
+        unsigned *w = reinterpret_cast<unsigned *>(&r);
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(s[2 * i], s[2 * i + 1]);
+                w[i] = *reinterpret_cast<const unsigned *>(&h);
+            } else {
+                const __half2 h = __floats2half2_rn(s[2 * i], s[2 * i + 1]);
+                w[i] = *reinterpret_cast<const unsigned *>(&h);
+            }
+        }
+        return r;
+    }
+}
+
+// One element: read-only load converted to the compute type / store rounded.
+template <typename T>
+__device__ __forceinline__ CT<T> load1(const T *p) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) return __ldg(p);
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    else
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
+}
+template <typename T>
+__device__ __forceinline__ CT<T> to_compute(T x) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) return x;
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(x);
+    else return __half2float(x);
+}
+template <typename T>
+__device__ __forceinline__ T to_storage(CT<T> x) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) return x;
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float2bfloat16_rn(x);
+    else return __float2half_rn(x);
+}
 
 // Gene in the form the update consumes.  The -4 centre weight of the
 // Laplacian is folded into the reaction coefficients (cm4 = c - 4 Du,
@@ -116,44 +229,33 @@ __device__ __forceinline__ void cell_update(T uc, T un, T us, T uw, T ue,
 }
 
 // A lane's slice of one grid row for both fields: V consecutive columns.
-template <typename T> struct Slice {
-    T u[Vec<T>::N];
-    T v[Vec<T>::N];
+template <typename T, int N = Vec<T>::N> struct Slice {
+    T u[N];
+    T v[N];
 };
 
-template <typename T>
-__device__ __forceinline__ void load_vec(T (&dst)[Vec<T>::N], const T *__restrict__ src) {
-    typedef typename Vec<T>::type VT;
+template <typename T, int V>
+__device__ __forceinline__ void load_vec(CT<T> (&dst)[V], const T *__restrict__ src) {
+    typedef typename LaneVec<T, V>::type VT;
     const VT x = __ldg(reinterpret_cast<const VT *>(src));
-    if constexpr (Vec<T>::N == 4) {
-        dst[0] = x.x; dst[1] = x.y; dst[2] = x.z; dst[3] = x.w;
-    } else {
-        dst[0] = x.x; dst[1] = x.y;
-    }
+    unpack_vec<T, V>(x, dst);
 }
 
-template <typename T>
-__device__ __forceinline__ void store_vec(T *__restrict__ dst, const T (&src)[Vec<T>::N]) {
-    typedef typename Vec<T>::type VT;
-    VT x;
-    if constexpr (Vec<T>::N == 4) {
-        x.x = src[0]; x.y = src[1]; x.z = src[2]; x.w = src[3];
-    } else {
-        x.x = src[0]; x.y = src[1];
-    }
-    *reinterpret_cast<VT *>(dst) = x;
+template <typename T, int V>
+__device__ __forceinline__ void store_vec(T *__restrict__ dst, const CT<T> (&src)[V]) {
+    typedef typename LaneVec<T, V>::type VT;
+    *reinterpret_cast<VT *>(dst) = pack_vec<T, V>(src);
 }
 
 // Stencil over one lane's slice.  cen = row i, nor = row i-1, sou = row i+1.
 // The west neighbour of element 0 and the east neighbour of element V-1 come
 // from the adjacent lanes (or, for lanes whose neighbour is not in the warp,
 // from the caller: west_u/east_u etc.).
-template <typename T, int RX>
-__device__ __forceinline__ void slice_update(const Slice<T> &nor, const Slice<T> &cen,
-                                             const Slice<T> &sou, T west_u, T east_u,
+template <typename T, int RX, int V = Vec<T>::N>
+__device__ __forceinline__ void slice_update(const Slice<T, V> &nor, const Slice<T, V> &cen,
+                                             const Slice<T, V> &sou, T west_u, T east_u,
                                              T west_v, T east_v, const Coef<T> &p,
-                                             Slice<T> &out) {
-    constexpr int V = Vec<T>::N;
+                                             Slice<T, V> &out) {
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const T wu = (e == 0) ? west_u : cen.u[e - 1];
@@ -188,17 +290,17 @@ inline Coef<T> make_coef(const rdcnn_params &p, int reaction) {
     return q;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_slice(Slice<T> &s, const T *__restrict__ u,
+template <typename T, int V = Vec<T>::N>
+__device__ __forceinline__ void load_slice(Slice<CT<T>, V> &s, const T *__restrict__ u,
                                            const T *__restrict__ v, int64_t off) {
     load_vec<T>(s.u, u + off);
     load_vec<T>(s.v, v + off);
 }
 
-template <typename T>
-__device__ __forceinline__ void zero_slice(Slice<T> &s) {
+template <typename T, int N>
+__device__ __forceinline__ void zero_slice(Slice<T, N> &s) {
 #pragma unroll
-    for (int e = 0; e < Vec<T>::N; ++e) {
+    for (int e = 0; e < N; ++e) {
         s.u[e] = T(0);
         s.v[e] = T(0);
     }

@@ -39,6 +39,8 @@ constexpr int kStep1Block = 256;
 
 // --------------------------------------------------------------------------- single step
 
+// FP32 / FP64 planes (16-bit planes take the ring-staged pipeline at k = 1,
+// see step1_t).
 template <typename T, int RX, int BC>
 __global__ void __launch_bounds__(kStep1Block)
 k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
@@ -130,7 +132,7 @@ k_temporal_split(const T *__restrict__ u, const T *__restrict__ v, T *__restrict
 template <typename T, int RX, int BC>
 __global__ void __launch_bounds__(256)
 k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
-          T *__restrict__ vn, int nn, int nm, Coef<T> p) {
+          T *__restrict__ vn, int nn, int nm, Coef<CT<T>> p) {
     constexpr bool zf = (BC == BC_MIRROR);
     const int64_t n = (int64_t)nn * nm;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
@@ -144,20 +146,21 @@ k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
         const int64_t ri = (int64_t)i * nm;
         const int64_t rp = (int64_t)ip * nm;
         const int64_t rm = (int64_t)im * nm;
-        T ou, ov;
-        cell_update<T, RX>(u[ri + j], u[rm + j], u[rp + j], u[ri + jm], u[ri + jp],
-                           v[ri + j], v[rm + j], v[rp + j], v[ri + jm], v[ri + jp], p, ou, ov);
-        un[idx] = ou;
-        vn[idx] = ov;
+        CT<T> ou, ov;
+        cell_update<CT<T>, RX>(load1(u + ri + j), load1(u + rm + j), load1(u + rp + j), load1(u + ri + jm),
+                               load1(u + ri + jp), load1(v + ri + j), load1(v + rm + j), load1(v + rp + j),
+                               load1(v + ri + jm), load1(v + ri + jp), p, ou, ov);
+        un[idx] = to_storage<T>(ou);
+        vn[idx] = to_storage<T>(ov);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_init(const T *__restrict__ x, T *u, T *v, T ka, int64_t n) {
+k_init(const T *x, T *u, T *v, CT<T> ka, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const T t = mul_rn(ka, x[i]);
+        const T t = to_storage<T>(mul_rn(ka, to_compute<T>(x[i])));  // x may alias u: plain loads
         u[i] = t;
         v[i] = t;
     }
@@ -166,19 +169,27 @@ k_init(const T *__restrict__ x, T *u, T *v, T ka, int64_t n) {
 template <typename T>
 cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, void *un, void *vn,
                     int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
-    constexpr int V = Vec<T>::N;
-    const int bands = (int)((nm + 32 * V - 1) / (32 * V));
-    const int strips = (int)((nn + rows - 1) / rows);
-    const int64_t nwarps = (int64_t)bands * strips;
-    const int wpb = kStep1Block / 32;
-    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    const Coef<T> c = make_coef<T>(p, reaction);
-    return with_model(reaction, boundary, [&](auto rx, auto bc) {
-        k_step1<T, decltype(rx)::value, decltype(bc)::value><<<grid, kStep1Block, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, rows, c);
-        count_launches(1);
-        return cudaGetLastError();
-    });
+    if constexpr (!is_wide<T>()) {
+        // 16-bit planes: a row carries half the bytes, and keeping HBM busy needs
+        // more rows in flight than the register prefetch above holds; the
+        // cp.async ring of the temporal pipeline at depth 1 keeps three per warp
+        // (same arithmetic, one rounding per step: the same bits).
+        return temporal_launch<T, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+    } else {
+        constexpr int V = Vec<T>::N;
+        const int bands = (int)((nm + 32 * V - 1) / (32 * V));
+        const int strips = (int)((nn + rows - 1) / rows);
+        const int64_t nwarps = (int64_t)bands * strips;
+        const int wpb = kStep1Block / 32;
+        const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
+        const Coef<T> c = make_coef<T>(p, reaction);
+        return with_model(reaction, boundary, [&](auto rx, auto bc) {
+            k_step1<T, decltype(rx)::value, decltype(bc)::value><<<grid, kStep1Block, 0, s>>>(
+                (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, rows, c);
+            count_launches(1);
+            return cudaGetLastError();
+        });
+    }
 }
 
 }  // namespace
@@ -263,7 +274,7 @@ cudaError_t generic_t(int reaction, int boundary, const void *u, const void *v, 
     const int64_t n = nn * nm;
     const int64_t want = (n + 255) / 256;
     const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)sm_count() * 16);
-    const Coef<T> c = make_coef<T>(p, reaction);
+    const Coef<CT<T>> c = make_coef<CT<T>>(p, reaction);
     return with_model(reaction, boundary, [&](auto rx, auto bc) {
         k_generic<T, decltype(rx)::value, decltype(bc)::value><<<grid, 256, 0, s>>>(
             (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, c);
@@ -285,115 +296,87 @@ int sm_count() {
 cudaError_t launch_step1(int dtype, int reaction, int boundary, const void *u, const void *v,
                          void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
                          cudaStream_t s) {
-    if (dtype == RDCNN_F64) return step1_t<double>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
-    return step1_t<float>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+    return with_dtype(dtype, [&](auto tag) {
+        return step1_t<decltype(tag)>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+    });
 }
 
 cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const void *u,
                             const void *v, void *un, void *vn, int64_t nn, int64_t nm,
                             const rdcnn_params &p, int rows, cudaStream_t s) {
-#define RDK_TL(TT, KK) temporal_launch<TT, KK>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s)
-    if (dtype == RDCNN_F64) {
-        switch (k) {
-            case 1: return RDK_TL(double, 1);
-            case 2: return RDK_TL(double, 2);
-            case 3: return RDK_TL(double, 3);
-            case 4: return RDK_TL(double, 4);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (k) {
-        case 1: return RDK_TL(float, 1);
-        case 2: return RDK_TL(float, 2);
-        case 3: return RDK_TL(float, 3);
-        case 4: return RDK_TL(float, 4);
-        case 5: return RDK_TL(float, 5);
-        case 6: return RDK_TL(float, 6);
-        case 7: return RDK_TL(float, 7);
-        case 8: return RDK_TL(float, 8);
-        default: return cudaErrorInvalidValue;
-    }
-#undef RDK_TL
+    return with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        return with_depth(k, [&](auto kk) -> cudaError_t {
+            constexpr int K = decltype(kk)::value;
+            if constexpr (K <= MaxDepth<T>::value)
+                return temporal_launch<T, K>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+            else
+                return cudaErrorInvalidValue;
+        });
+    });
 }
 
-// Periodic FitzHugh-Nagumo / pure diffusion only (the caller checks).
+// FP32 / FP64 storage, periodic FitzHugh-Nagumo / pure diffusion only (the caller checks).
 cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                                   int rows, cudaStream_t s) {
     if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE) return cudaErrorInvalidValue;
-    if (dtype == RDCNN_F64) {
-        switch (k) {
-            case 2: return split_tk<double, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            case 3: return split_tk<double, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            case 4: return split_tk<double, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (k) {
-        case 2: return split_tk<float, 2>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 3: return split_tk<float, 3>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 4: return split_tk<float, 4>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 5: return split_tk<float, 5>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 6: return split_tk<float, 6>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 7: return split_tk<float, 7>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        case 8: return split_tk<float, 8>(reaction, u, v, un, vn, nn, nm, p, rows, s);
-        default: return cudaErrorInvalidValue;
-    }
+    if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return cudaErrorInvalidValue;
+    return with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        return with_depth(k, [&](auto kk) -> cudaError_t {
+            constexpr int K = decltype(kk)::value;
+            if constexpr (K >= 2 && K <= MaxDepth<T>::value &&
+                          (std::is_same<T, float>::value || std::is_same<T, double>::value))
+                return split_tk<T, K>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+            else
+                return cudaErrorInvalidValue;
+        });
+    });
 }
 
 cudaError_t launch_generic(int dtype, int reaction, int boundary, const void *u, const void *v,
                            void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                            cudaStream_t s) {
-    if (dtype == RDCNN_F64) return generic_t<double>(reaction, boundary, u, v, un, vn, nn, nm, p, s);
-    return generic_t<float>(reaction, boundary, u, v, un, vn, nn, nm, p, s);
+    return with_dtype(dtype, [&](auto tag) {
+        return generic_t<decltype(tag)>(reaction, boundary, u, v, un, vn, nn, nm, p, s);
+    });
 }
 
 cudaError_t launch_init(int dtype, const void *x, void *u, void *v, double ka, int64_t n,
                         cudaStream_t s) {
     const int64_t want = (n + 255) / 256;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 16));
-    if (dtype == RDCNN_F64)
-        k_init<double><<<grid, 256, 0, s>>>((const double *)x, (double *)u, (double *)v, ka, n);
-    else
-        k_init<float><<<grid, 256, 0, s>>>((const float *)x, (float *)u, (float *)v, (float)ka, n);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template <typename T, int K>
-int plan_rows_k(int reaction, int boundary, int variant, int64_t nn, int64_t nm, int rows) {
-    if constexpr (K >= 2) {
-        if (variant == RDCNN_VARIANT_TEMPORAL2) return split_rows<T, K>(reaction, nn, nm, rows);
-    }
-    return temporal_rows<T, K>(reaction, boundary, nn, nm, rows);
+    return with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        k_init<T><<<grid, 256, 0, s>>>((const T *)x, (T *)u, (T *)v, (CT<T>)ka, n);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t nn, int64_t nm,
               int rows) {
     if (variant == RDCNN_VARIANT_STEP1) return rows > 0 ? rows : default_rows_step1(dtype, nn, nm);
     if (variant == RDCNN_VARIANT_GENERIC) return 0;
-#define RDK_PR(TT, KK) plan_rows_k<TT, KK>(reaction, boundary, variant, nn, nm, rows)
-    if (dtype == RDCNN_F64) {
-        switch (k) {
-            case 1: return RDK_PR(double, 1);
-            case 2: return RDK_PR(double, 2);
-            case 3: return RDK_PR(double, 3);
-            case 4: return RDK_PR(double, 4);
-            default: return 0;
-        }
-    }
-    switch (k) {
-        case 1: return RDK_PR(float, 1);
-        case 2: return RDK_PR(float, 2);
-        case 3: return RDK_PR(float, 3);
-        case 4: return RDK_PR(float, 4);
-        case 5: return RDK_PR(float, 5);
-        case 6: return RDK_PR(float, 6);
-        case 7: return RDK_PR(float, 7);
-        case 8: return RDK_PR(float, 8);
-        default: return 0;
-    }
-#undef RDK_PR
+    int out = 0;
+    with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        return with_depth(k, [&](auto kk) -> cudaError_t {
+            constexpr int K = decltype(kk)::value;
+            if constexpr (K <= MaxDepth<T>::value) {
+                if constexpr (K >= 2 && (std::is_same<T, float>::value || std::is_same<T, double>::value)) {
+                    if (variant == RDCNN_VARIANT_TEMPORAL2) {
+                        out = split_rows<T, K>(reaction, nn, nm, rows);
+                        return cudaSuccess;
+                    }
+                }
+                out = temporal_rows<T, K>(reaction, boundary, nn, nm, rows);
+            }
+            return cudaSuccess;
+        });
+    });
+    return out;
 }
 
 // Temporal depth by grid size, from a launch-shape sweep on GB300 (FP32,
@@ -411,10 +394,12 @@ int default_k(int dtype, int64_t nn, int64_t nm) {
     return std::min(k, max_k(dtype));
 }
 
-// The single-step kernel is fastest with short strips (more warps in flight).
+// The single-step kernel is fastest with short strips (more warps in flight);
+// the 16-bit single step (the ring pipeline at depth 1) with 16-row strips
+// (measured at 4096^2: 4 rows 480, 16 rows 580-620 Gcell/s).
 int default_rows_step1(int dtype, int64_t nn, int64_t nm) {
-    (void)dtype; (void)nn; (void)nm;
-    return 4;
+    (void)nn; (void)nm;
+    return is_16bit(dtype) ? 16 : 4;
 }
 
 }  // namespace rdk

@@ -29,7 +29,17 @@ constexpr int kMaxK32 = 8;  // temporal depth, FP32
 constexpr int kMaxK64 = 4;  // temporal depth, FP64
 
 inline int vec_width(int dtype) { return dtype == RDCNN_F64 ? 2 : 4; }
-inline size_t elem_size(int dtype) { return dtype == RDCNN_F64 ? 8 : 4; }
+inline size_t elem_size(int dtype) {
+    return dtype == RDCNN_F64 ? 8 : (dtype == RDCNN_BF16 || dtype == RDCNN_F16) ? 2 : 4;
+}
+inline bool is_16bit(int dtype) { return dtype == RDCNN_BF16 || dtype == RDCNN_F16; }
+// Alignment the vectorised kernels need: one lane vector of the temporal
+// pipeline (16 bytes; 8 bytes = 4 values for 16-bit planes).
+inline size_t vec_align(int dtype) { return is_16bit(dtype) ? 8 : 16; }
+// Byte offset of the second ping-pong plane in a handle's workspace: the
+// plane size rounded up to 256 bytes, so that both planes share the
+// workspace's alignment whatever the grid size.
+inline size_t plane_stride(size_t plane_bytes) { return (plane_bytes + 255) & ~(size_t)255; }
 inline int max_k(int dtype) { return dtype == RDCNN_F64 ? kMaxK64 : kMaxK32; }
 
 // Columns of output a warp of the temporal kernel produces for depth k.
@@ -49,6 +59,7 @@ int cuda_error(cudaError_t e, const char *what);
 // has no diffusion stability bound.
 int check_params(const rdcnn_params *p, int reaction = RDCNN_REACTION_FHN);
 bool aligned16(const void *p);
+inline bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 int sm_count();
 
 // Read-only view of a handle's configuration (defined in api.cu); the stream

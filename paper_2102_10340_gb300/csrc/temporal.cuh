@@ -36,6 +36,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// 8-byte variant (16-bit storage: 4 values per lane); cp.async.cg takes 16 only.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -53,33 +58,33 @@ __device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, in
                                            const T *__restrict__ u, const T *__restrict__ v) {
     const int lane = threadIdx.x & 31;
     const int64_t off = (int64_t)g * nm + lc;
-    cp_async16(&r.slot[m % kRing][0][lane], u + off);
-    cp_async16(&r.slot[m % kRing][1][lane], v + off);
+    if constexpr (sizeof(typename Vec<T>::type) == 16) {
+        cp_async16(&r.slot[m % kRing][0][lane], u + off);
+        cp_async16(&r.slot[m % kRing][1][lane], v + off);
+    } else {
+        cp_async8(&r.slot[m % kRing][0][lane], u + off);
+        cp_async8(&r.slot[m % kRing][1][lane], v + off);
+    }
 }
 
 template <typename T>
-__device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<T> &s) {
+__device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<CT<T>> &s) {
     typedef typename Vec<T>::type VT;
     const int lane = threadIdx.x & 31;
     const VT a = r.slot[m % kRing][0][lane];
     const VT b = r.slot[m % kRing][1][lane];
-    if constexpr (Vec<T>::N == 4) {
-        s.u[0] = a.x; s.u[1] = a.y; s.u[2] = a.z; s.u[3] = a.w;
-        s.v[0] = b.x; s.v[1] = b.y; s.v[2] = b.z; s.v[3] = b.w;
-    } else {
-        s.u[0] = a.x; s.u[1] = a.y;
-        s.v[0] = b.x; s.v[1] = b.y;
-    }
+    unpack_vec<T, Vec<T>::N>(a, s.u);
+    unpack_vec<T, Vec<T>::N>(b, s.v);
 }
 
 // ring_read for boundary BC; under BC_MIRROR a lane whose columns lie beyond
 // an edge (rev) reverses the element order of the mirrored vector it loaded.
 template <typename T, int BC>
-__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<T> &s) {
+__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<CT<T>> &s) {
     ring_read(r, m, s);
     if constexpr (BC == BC_MIRROR) {
         constexpr int V = Vec<T>::N;
-        Slice<T> t = s;
+        Slice<CT<T>> t = s;
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             s.u[e] = rev ? t.u[V - 1 - e] : t.u[e];
@@ -130,7 +135,7 @@ template <int BC> struct RowWalk {
 //        its output (q = input-row index within the strip, see temporal_strip)
 //   P::finish(q, out)                    the row q leaving the last stage
 template <typename T, int K, int PH, int BC, class P>
-__device__ __forceinline__ void pipeline_beat(int m, int total, Slice<T> (&W)[3][K],
+__device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>> (&W)[3][K],
                                               const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
                                               int lc, bool rev, const T *__restrict__ u,
                                               const T *__restrict__ v, P &pol) {
@@ -145,18 +150,18 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<T> (&W)[3]
     }
     cp_async_commit();
     cp_async_wait<kRing - 1>();  // the group holding row m is complete
-    Slice<T> cur;
+    Slice<CT<T>> cur;
     ring_read_bc<T, BC>(ring, m, rev, cur);
     pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        Slice<T> &A = W[PH][s];
-        Slice<T> &B = W[(PH + 1) % 3][s];
-        const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
-        const T eu = __shfl_down_sync(kFull, B.u[0], 1);
-        const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
-        const T ev = __shfl_down_sync(kFull, B.v[0], 1);
-        Slice<T> out;
+        Slice<CT<T>> &A = W[PH][s];
+        Slice<CT<T>> &B = W[(PH + 1) % 3][s];
+        const CT<T> wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
+        const CT<T> eu = __shfl_down_sync(kFull, B.u[0], 1);
+        const CT<T> wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
+        const CT<T> ev = __shfl_down_sync(kFull, B.v[0], 1);
+        Slice<CT<T>> out;
         pol.stage(s, A, B, cur, wu, eu, wv, ev, m - s - 1, out);
         W[(PH + 2) % 3][s] = cur;
         cur = out;
@@ -207,7 +212,7 @@ __device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int
 template <typename T, int K, int BC = BC_WRAP, class P>
 __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__restrict__ u,
                                                const T *__restrict__ v, int nn, int nm, P &pol) {
-    Slice<T> W[3][K];
+    Slice<CT<T>> W[3][K];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -241,18 +246,18 @@ __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__
 // Forward policy: Eq. 1 at every stage; the last stage's owned rows are stored.
 template <typename T, int K, int RX>
 struct ForwardPolicy {
-    const Coef<T> &p;
+    const Coef<CT<T>> &p;
     const StripGeom &geo;
     T *__restrict__ un;
     T *__restrict__ vn;
     int nm;
     __device__ __forceinline__ void issue(int) {}
     __device__ __forceinline__ void begin_beat(int) {}
-    __device__ __forceinline__ void stage(int, const Slice<T> &A, const Slice<T> &B, const Slice<T> &C,
-                                          T wu, T eu, T wv, T ev, int, Slice<T> &out) {
-        slice_update<T, RX>(A, B, C, wu, eu, wv, ev, p, out);
+    __device__ __forceinline__ void stage(int, const Slice<CT<T>> &A, const Slice<CT<T>> &B, const Slice<CT<T>> &C,
+                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int, Slice<CT<T>> &out) {
+        slice_update<CT<T>, RX>(A, B, C, wu, eu, wv, ev, p, out);
     }
-    __device__ __forceinline__ void finish(int q, const Slice<T> &out) {
+    __device__ __forceinline__ void finish(int q, const Slice<CT<T>> &out) {
         const int orow = q - K;
         if (orow >= 0 && geo.st_lane) {
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
@@ -273,15 +278,15 @@ template <typename T> struct StagePlanes {
 // needs, K per launch.
 template <typename T, int K, int RX>
 struct ForwardAllPolicy {
-    const Coef<T> &p;
+    const Coef<CT<T>> &p;
     const StripGeom &geo;
     const StagePlanes<T> &planes;
     int nm;
     __device__ __forceinline__ void issue(int) {}
     __device__ __forceinline__ void begin_beat(int) {}
-    __device__ __forceinline__ void stage(int s, const Slice<T> &A, const Slice<T> &B, const Slice<T> &C,
-                                          T wu, T eu, T wv, T ev, int q, Slice<T> &out) {
-        slice_update<T, RX>(A, B, C, wu, eu, wv, ev, p, out);
+    __device__ __forceinline__ void stage(int s, const Slice<CT<T>> &A, const Slice<CT<T>> &B, const Slice<CT<T>> &C,
+                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int q, Slice<CT<T>> &out) {
+        slice_update<CT<T>, RX>(A, B, C, wu, eu, wv, ev, p, out);
         const int orow = q - K;
         if (orow >= 0 && orow < geo.nout && geo.st_lane) {
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
@@ -289,7 +294,7 @@ struct ForwardAllPolicy {
             store_vec<T>(planes.v[s] + off, out.v);
         }
     }
-    __device__ __forceinline__ void finish(int, const Slice<T> &) {}
+    __device__ __forceinline__ void finish(int, const Slice<CT<T>> &) {}
 };
 
 // H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
@@ -299,7 +304,7 @@ template <typename T, int K, int H, int RX, int BC = BC_WRAP>
 __device__ __forceinline__ void temporal_strip(int band, int strip, const T *__restrict__ u,
                                                const T *__restrict__ v, T *__restrict__ un,
                                                T *__restrict__ vn, int nn, int nm, int rows,
-                                               const Coef<T> &p) {
+                                               const Coef<CT<T>> &p) {
     const StripGeom geo = strip_geom<T, K, H, BC>(band, strip, nn, nm, rows);
     ForwardPolicy<T, K, RX> pol{p, geo, un, vn, nm};
     pipeline_strip<T, K, BC>(geo, u, v, nn, nm, pol);
@@ -312,7 +317,7 @@ constexpr int kTemporalBlock = 32 * kTemporalWarps;
 template <typename T, int K, int RX, int BC>
 __global__ void __launch_bounds__(kTemporalBlock)
 k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
-           T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
+           T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<CT<T>> p) {
     const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;  // whole warps only
     constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;

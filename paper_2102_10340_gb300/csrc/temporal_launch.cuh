@@ -48,7 +48,7 @@ cudaError_t temporal_launch(int reaction, int boundary, const void *u, const voi
                             void *vn, int64_t nn, int64_t nm, const rdcnn_params &p, int rows,
                             cudaStream_t s) {
     const int bands = temporal_bands<T, K>(nm);
-    const Coef<T> c = make_coef<T>(p, reaction);
+    const Coef<CT<T>> c = make_coef<CT<T>>(p, reaction);
     const int r = temporal_rows<T, K>(reaction, boundary, nn, nm, rows);
     return with_model(reaction, boundary, [&](auto rx, auto bc) {
         constexpr int RX = decltype(rx)::value;

@@ -30,11 +30,12 @@ _BOUNDARIES = {"periodic": L.BC_PERIODIC, "zeroflux": L.BC_ZEROFLUX}
 
 
 def _dtype_code(dtype: torch.dtype) -> int:
-    if dtype == torch.float32:
-        return L.F32
-    if dtype == torch.float64:
-        return L.F64
-    raise TypeError(f"unsupported dtype {dtype}: use torch.float32 or torch.float64")
+    """Plane type: float32 / float64, or 16-bit storage (bfloat16 / float16) with FP32 arithmetic
+    and the state rounded once per launch (every k steps of the temporal variant)."""
+    codes = {torch.float32: L.F32, torch.float64: L.F64, torch.bfloat16: L.BF16, torch.float16: L.F16}
+    if dtype not in codes:
+        raise TypeError(f"unsupported dtype {dtype}: use float32, float64, bfloat16 or float16")
+    return codes[dtype]
 
 
 def _stream_ptr(device) -> int:

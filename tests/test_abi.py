@@ -97,7 +97,8 @@ def test_unbound_handle_and_workspace(lib, L):
     rc, h = _create(lib, L, nn=6, nm=10, dtype=L.F64)
     n = ctypes.c_size_t()
     assert lib.rdcnn_workspace_bytes(h, ctypes.byref(n)) == L.OK
-    assert n.value == 2 * 6 * 10 * 8
+    plane = 6 * 10 * 8
+    assert n.value == ((plane + 255) // 256) * 256 + plane  # second plane 256-byte aligned
     assert lib.rdcnn_run(h, 5, 0, 0) == L.ESTATE
     assert lib.rdcnn_get_state(h, None, None, 0) == L.ESTATE
     assert lib.rdcnn_init(h, None, 1.0, 1) == L.ESTATE
@@ -117,7 +118,7 @@ def test_unbound_handle_and_workspace(lib, L):
 def test_bound_run_rejects_bad_args_before_gpu_work(lib, L):
     rc, h = _create(lib, L, nn=4, nm=6)
     # fake, never-dereferenced addresses: validation must fail before any CUDA call
-    assert lib.rdcnn_bind(h, 256, 512, 1024, 4 * 6 * 4 * 2, None) == L.OK
+    assert lib.rdcnn_bind(h, 256, 512, 1024, 256 + 4 * 6 * 4, None) == L.OK
     assert lib.rdcnn_run(h, -1, 0, 0) == L.EINVAL
     assert lib.rdcnn_run(h, 5, 9, 0) == L.EINVAL
     assert lib.rdcnn_run(h, 5, L.VARIANT_TEMPORAL, 0) == L.EINVAL  # NM=6 is not a multiple of 4
@@ -172,7 +173,7 @@ def header_enums():
 
 def test_binding_constants_match_header(L):
     enums = header_enums()
-    for name in ("BC_PERIODIC", "BC_ZEROFLUX", "F32", "F64", "REACTION_FHN", "REACTION_NONE",
+    for name in ("BC_PERIODIC", "BC_ZEROFLUX", "F32", "F64", "BF16", "F16", "REACTION_FHN", "REACTION_NONE",
                  "REACTION_CENN", "VARIANT_AUTO", "VARIANT_STEP1", "VARIANT_TEMPORAL",
                  "VARIANT_GENERIC", "VARIANT_TEMPORAL2"):
         assert getattr(L, name) == enums[name], name
@@ -216,3 +217,17 @@ def test_plan_resolves_without_running(lib, L):
     var = ctypes.c_int(L.VARIANT_TEMPORAL2)
     assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(L.Tune(4, 0))) == L.EINVAL
     lib.rdcnn_destroy(h)
+
+
+def test_create_accepts_16bit_storage(lib, L):
+    for dt in (L.BF16, L.F16):
+        rc, h = _create(lib, L, nn=16, nm=16, dtype=dt)
+        assert rc == 0
+        nbytes = ctypes.c_size_t()
+        assert lib.rdcnn_workspace_bytes(h, ctypes.byref(nbytes)) == 0 and nbytes.value == 512 + 16 * 16 * 2
+        var = ctypes.c_int(L.VARIANT_TEMPORAL2)
+        assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(L.Tune(4, 0))) == L.EINVAL
+        nbytes = ctypes.c_size_t()
+        assert lib.rdcnn_adjoint_workspace_bytes(h, 10, 0, ctypes.byref(nbytes)) == L.EINVAL
+        lib.rdcnn_destroy(h)
+    assert _create(lib, L, dtype=4)[0] == L.EINVAL
