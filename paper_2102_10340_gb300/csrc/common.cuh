@@ -86,12 +86,27 @@ template <> struct LaneVec<double, 2> { typedef double2 type; };
 template <> struct LaneVec<__nv_bfloat16, 4> { typedef uint2 type; };
 template <> struct LaneVec<__half, 4> { typedef uint2 type; };
 
+// A 16-bit storage type read 8 values (16 bytes) per lane: the same bits in
+// memory as E, a distinct type so that a pipeline instantiated on it takes
+// the wider lane (the depth-1 pipeline of 16-bit planes, where the fixed
+// per-row costs of a lane then cover twice the cells).
+template <typename E> struct Wide16 { E x; };
+template <typename E> struct LaneVec<Wide16<E>, 8> { typedef uint4 type; };
+
+// The 16-bit format behind a storage type (itself for the plain types).
+template <typename T> struct Base16 { typedef T type; };
+template <typename E> struct Base16<Wide16<E>> { typedef E type; };
+
 // Lane width of the register pipelines: 4 values (2 doubles) of every
 // storage type, so that 16-bit planes share the FP32 lane layout and
-// register budget (8 bytes per lane and field).
+// register budget (8 bytes per lane and field); 8 for Wide16.
 template <typename T> struct Vec {
     static constexpr int N = std::is_same<T, double>::value ? 2 : 4;
     typedef typename LaneVec<T, N>::type type;
+};
+template <typename E> struct Vec<Wide16<E>> {
+    static constexpr int N = 8;
+    typedef uint4 type;
 };
 
 // Arithmetic type of a storage type: 16-bit planes are computed in FP32 and
@@ -99,10 +114,12 @@ template <typename T> struct Vec {
 template <typename T> struct Compute { typedef T type; };
 template <> struct Compute<__nv_bfloat16> { typedef float type; };
 template <> struct Compute<__half> { typedef float type; };
+template <typename E> struct Compute<Wide16<E>> { typedef float type; };
 template <typename T> using CT = typename Compute<T>::type;
 
+// float / double planes: arithmetic in the storage type itself.
 template <typename T>
-constexpr bool is_wide() { return std::is_same<T, float>::value || std::is_same<T, double>::value; }
+constexpr bool is_f32_f64() { return std::is_same<T, float>::value || std::is_same<T, double>::value; }
 
 // Storage vector <-> compute values.
 template <typename T, int V>
@@ -116,7 +133,7 @@ __device__ __forceinline__ void unpack_vec(const typename LaneVec<T, V>::type &x
 #pragma unroll
         for (int i = 0; i < V / 2; ++i) {
             float2 f;
-            if constexpr (std::is_same<T, __nv_bfloat16>::value)
+            if constexpr (std::is_same<typename Base16<T>::type, __nv_bfloat16>::value)
                 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[i]));
             else
                 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
@@ -136,7 +153,7 @@ __device__ __forceinline__ typename LaneVec<T, V>::type pack_vec(const CT<T> (&s
         unsigned *w = reinterpret_cast<unsigned *>(&r);
 #pragma unroll
         for (int i = 0; i < V / 2; ++i) {
-            if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+            if constexpr (std::is_same<typename Base16<T>::type, __nv_bfloat16>::value) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(s[2 * i], s[2 * i + 1]);
                 w[i] = *reinterpret_cast<const unsigned *>(&h);
             } else {

@@ -169,11 +169,14 @@ k_init(const T *x, T *u, T *v, CT<T> ka, int64_t n) {
 template <typename T>
 cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, void *un, void *vn,
                     int64_t nn, int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
-    if constexpr (!is_wide<T>()) {
+    if constexpr (!is_f32_f64<T>()) {
         // 16-bit planes: a row carries half the bytes, and keeping HBM busy needs
         // more rows in flight than the register prefetch above holds; the
         // cp.async ring of the temporal pipeline at depth 1 keeps three per warp
-        // (same arithmetic, one rounding per step: the same bits).
+        // (same arithmetic, one rounding per step: the same bits), with 8 values
+        // (16 bytes) per lane when NM and the alignment allow.
+        if (nm % 8 == 0 && aligned16(u) && aligned16(v) && aligned16(un) && aligned16(vn))
+            return temporal_launch<Wide16<T>, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
         return temporal_launch<T, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
     } else {
         constexpr int V = Vec<T>::N;
@@ -327,7 +330,7 @@ cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u,
         return with_depth(k, [&](auto kk) -> cudaError_t {
             constexpr int K = decltype(kk)::value;
             if constexpr (K >= 2 && K <= MaxDepth<T>::value &&
-                          (std::is_same<T, float>::value || std::is_same<T, double>::value))
+                          is_f32_f64<T>())
                 return split_tk<T, K>(reaction, u, v, un, vn, nn, nm, p, rows, s);
             else
                 return cudaErrorInvalidValue;
@@ -365,7 +368,7 @@ int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t
         return with_depth(k, [&](auto kk) -> cudaError_t {
             constexpr int K = decltype(kk)::value;
             if constexpr (K <= MaxDepth<T>::value) {
-                if constexpr (K >= 2 && (std::is_same<T, float>::value || std::is_same<T, double>::value)) {
+                if constexpr (K >= 2 && is_f32_f64<T>()) {
                     if (variant == RDCNN_VARIANT_TEMPORAL2) {
                         out = split_rows<T, K>(reaction, nn, nm, rows);
                         return cudaSuccess;
@@ -395,11 +398,12 @@ int default_k(int dtype, int64_t nn, int64_t nm) {
 }
 
 // The single-step kernel is fastest with short strips (more warps in flight);
-// the 16-bit single step (the ring pipeline at depth 1) with 16-row strips
-// (measured at 4096^2: 4 rows 480, 16 rows 580-620 Gcell/s).
+// the 16-bit single step (the ring pipeline at depth 1, 8 values per lane)
+// with 32-row strips (measured at 4096^2, bf16: 4 / 8 / 16 / 32 / 64 rows =
+// 507 / 570 / 627 / 672 / 574 Gcell/s).
 int default_rows_step1(int dtype, int64_t nn, int64_t nm) {
     (void)nn; (void)nm;
-    return is_16bit(dtype) ? 16 : 4;
+    return is_16bit(dtype) ? 32 : 4;
 }
 
 }  // namespace rdk

@@ -68,7 +68,7 @@ __device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, in
 }
 
 template <typename T>
-__device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<CT<T>> &s) {
+__device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<CT<T>, Vec<T>::N> &s) {
     typedef typename Vec<T>::type VT;
     const int lane = threadIdx.x & 31;
     const VT a = r.slot[m % kRing][0][lane];
@@ -80,11 +80,11 @@ __device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<CT<T
 // ring_read for boundary BC; under BC_MIRROR a lane whose columns lie beyond
 // an edge (rev) reverses the element order of the mirrored vector it loaded.
 template <typename T, int BC>
-__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<CT<T>> &s) {
+__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<CT<T>, Vec<T>::N> &s) {
     ring_read(r, m, s);
     if constexpr (BC == BC_MIRROR) {
         constexpr int V = Vec<T>::N;
-        Slice<CT<T>> t = s;
+        Slice<CT<T>, Vec<T>::N> t = s;
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             s.u[e] = rev ? t.u[V - 1 - e] : t.u[e];
@@ -135,7 +135,7 @@ template <int BC> struct RowWalk {
 //        its output (q = input-row index within the strip, see temporal_strip)
 //   P::finish(q, out)                    the row q leaving the last stage
 template <typename T, int K, int PH, int BC, class P>
-__device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>> (&W)[3][K],
+__device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec<T>::N> (&W)[3][K],
                                               const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
                                               int lc, bool rev, const T *__restrict__ u,
                                               const T *__restrict__ v, P &pol) {
@@ -150,18 +150,18 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>> (&W
     }
     cp_async_commit();
     cp_async_wait<kRing - 1>();  // the group holding row m is complete
-    Slice<CT<T>> cur;
+    Slice<CT<T>, Vec<T>::N> cur;
     ring_read_bc<T, BC>(ring, m, rev, cur);
     pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        Slice<CT<T>> &A = W[PH][s];
-        Slice<CT<T>> &B = W[(PH + 1) % 3][s];
+        Slice<CT<T>, Vec<T>::N> &A = W[PH][s];
+        Slice<CT<T>, Vec<T>::N> &B = W[(PH + 1) % 3][s];
         const CT<T> wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
         const CT<T> eu = __shfl_down_sync(kFull, B.u[0], 1);
         const CT<T> wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
         const CT<T> ev = __shfl_down_sync(kFull, B.v[0], 1);
-        Slice<CT<T>> out;
+        Slice<CT<T>, Vec<T>::N> out;
         pol.stage(s, A, B, cur, wu, eu, wv, ev, m - s - 1, out);
         W[(PH + 2) % 3][s] = cur;
         cur = out;
@@ -212,7 +212,7 @@ __device__ __forceinline__ StripGeom strip_geom(int band, int strip, int nn, int
 template <typename T, int K, int BC = BC_WRAP, class P>
 __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__restrict__ u,
                                                const T *__restrict__ v, int nn, int nm, P &pol) {
-    Slice<CT<T>> W[3][K];
+    Slice<CT<T>, Vec<T>::N> W[3][K];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -253,11 +253,11 @@ struct ForwardPolicy {
     int nm;
     __device__ __forceinline__ void issue(int) {}
     __device__ __forceinline__ void begin_beat(int) {}
-    __device__ __forceinline__ void stage(int, const Slice<CT<T>> &A, const Slice<CT<T>> &B, const Slice<CT<T>> &C,
-                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int, Slice<CT<T>> &out) {
-        slice_update<CT<T>, RX>(A, B, C, wu, eu, wv, ev, p, out);
+    __device__ __forceinline__ void stage(int, const Slice<CT<T>, Vec<T>::N> &A, const Slice<CT<T>, Vec<T>::N> &B, const Slice<CT<T>, Vec<T>::N> &C,
+                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int, Slice<CT<T>, Vec<T>::N> &out) {
+        slice_update<CT<T>, RX, Vec<T>::N>(A, B, C, wu, eu, wv, ev, p, out);
     }
-    __device__ __forceinline__ void finish(int q, const Slice<CT<T>> &out) {
+    __device__ __forceinline__ void finish(int q, const Slice<CT<T>, Vec<T>::N> &out) {
         const int orow = q - K;
         if (orow >= 0 && geo.st_lane) {
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
@@ -284,9 +284,9 @@ struct ForwardAllPolicy {
     int nm;
     __device__ __forceinline__ void issue(int) {}
     __device__ __forceinline__ void begin_beat(int) {}
-    __device__ __forceinline__ void stage(int s, const Slice<CT<T>> &A, const Slice<CT<T>> &B, const Slice<CT<T>> &C,
-                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int q, Slice<CT<T>> &out) {
-        slice_update<CT<T>, RX>(A, B, C, wu, eu, wv, ev, p, out);
+    __device__ __forceinline__ void stage(int s, const Slice<CT<T>, Vec<T>::N> &A, const Slice<CT<T>, Vec<T>::N> &B, const Slice<CT<T>, Vec<T>::N> &C,
+                                          CT<T> wu, CT<T> eu, CT<T> wv, CT<T> ev, int q, Slice<CT<T>, Vec<T>::N> &out) {
+        slice_update<CT<T>, RX, Vec<T>::N>(A, B, C, wu, eu, wv, ev, p, out);
         const int orow = q - K;
         if (orow >= 0 && orow < geo.nout && geo.st_lane) {
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
@@ -294,7 +294,7 @@ struct ForwardAllPolicy {
             store_vec<T>(planes.v[s] + off, out.v);
         }
     }
-    __device__ __forceinline__ void finish(int, const Slice<CT<T>> &) {}
+    __device__ __forceinline__ void finish(int, const Slice<CT<T>, Vec<T>::N> &) {}
 };
 
 // H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than

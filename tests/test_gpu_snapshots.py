@@ -82,3 +82,21 @@ def test_snapshot_argument_errors(rd):
     hu = torch.empty((3, 8, 8), dtype=F32)
     rc = g.lib.rdcnn_run_snapshots(g.h, 10, 5, hu.data_ptr(), hu.data_ptr(), 0, None, 0)
     assert rc == L.ESPACE
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32], ids=["bf16", "f32"])
+def test_snapshots_of_model_variants(rd, dtype):
+    """A zero-flux CeNN grid (16-bit or FP32 planes): the captures equal separate runs.  Launches
+    end at multiples of `every`, so with `every` a multiple of the depth the 16-bit rounding
+    schedule is the plain run's too."""
+    gene = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.2, "Du": 0.1, "Dv": 0.0}
+    x = (1.5 * inp.uniform_field(8, 96, 128)).astype(np.float32)
+    w = (0.3 * inp.uniform_field(9, 96, 128)).astype(np.float32)
+    g = rd.Grid(96, 128, gene, dtype=dtype, reaction="cenn", boundary="zeroflux")
+    g.set_state(torch.from_numpy(x).to("cuda", dtype), torch.from_numpy(w).to("cuda", dtype))
+    us, vs = g.run_snapshots(48, 8, out="host", n_stage=2)
+    for s in range(7):
+        ru, rv = gpu_run(rd, torch.from_numpy(x).to(dtype).double().numpy(),
+                         torch.from_numpy(w).to(dtype).double().numpy(), gene, 8 * s, dtype, "auto",
+                         reaction="cenn", boundary="zeroflux")
+        assert np.array_equal(us[s].double().numpy(), ru) and np.array_equal(vs[s].double().numpy(), rv), s
