@@ -538,7 +538,7 @@ def run_ours(args):
 
     peaks = load_peaks()
     # roofline of the dominant kernel (one launch advances k steps over the whole grid)
-    fused = variant in ("temporal", "temporal2")
+    fused = variant in ("temporal", "temporal2", "temporal_wide")
     k = tune["k"] if fused else 1
     launch_ms = measure_launch_ms(rd, grid, variant, k, 2, 20, torch)
     cells = N * N
@@ -547,7 +547,8 @@ def run_ours(args):
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = flops / (launch_ms * 1e-3) / 1e12
-        kname = "k_temporal" if variant == "temporal" else "k_temporal_split"
+        kname = {"temporal": "k_temporal", "temporal2": "k_temporal_split",
+                 "temporal_wide": "k_temporal_wide"}[variant]
         traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md", k, plan["rows"]) if N == 4096
                          else (None, "other grid"))
         roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
@@ -614,7 +615,8 @@ def main(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
     ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage"), default=None,
                     help="run only this follow-on measurement (small, for profiling) and print it")
-    ap.add_argument("--variant", default="temporal", choices=("temporal", "temporal2", "step1", "generic"))
+    ap.add_argument("--variant", default="temporal",
+                    choices=("temporal", "temporal2", "temporal_wide", "step1", "generic"))
     ap.add_argument("--k", type=int, default=8)
     ap.add_argument("--rows", type=int, default=128)
     args = ap.parse_args(argv)

@@ -95,7 +95,8 @@ enum { RDCNN_VARIANT_AUTO = 0,                    /* library's choice (temporal 
        RDCNN_VARIANT_STEP1 = 1,                   /* one launch per time step, float4/double2 rows */
        RDCNN_VARIANT_TEMPORAL = 2,                /* k time steps fused per launch */
        RDCNN_VARIANT_GENERIC = 3,                 /* scalar path: any size, any alignment */
-       RDCNN_VARIANT_TEMPORAL2 = 4 };             /* temporal, the k stages split over two warps */
+       RDCNN_VARIANT_TEMPORAL2 = 4,               /* temporal, the k stages split over two warps */
+       RDCNN_VARIANT_TEMPORAL_WIDE = 5 };         /* temporal, 8 values per lane (k <= 4; not F64) */
 
 /* Launch shape: k = time steps fused per launch of the temporal kernels
  * (1..8 F32, 1..4 F64; 0 = library default), rows = grid rows each warp
@@ -168,6 +169,14 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
  * except RDCNN_VARIANT_TEMPORAL2, which returns RDCNN_EINVAL for ZEROFLUX
  * or CENN handles.  Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
 int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k);
+
+/* RDCNN_VARIANT_TEMPORAL_WIDE: the temporal pipeline with 8 values per lane
+ * (32 bytes of float, 16 of a 16-bit type) instead of 4, so one halo lane per
+ * side serves every depth and the per-row costs of a lane cover twice the
+ * cells; the register windows double, so k is limited to 1..4.  Needs NM % 8
+ * == 0 and 16-byte aligned buffers (RDCNN_EINVAL otherwise, as for the other
+ * explicit vectorised variants); not for RDCNN_F64.  Same bits as TEMPORAL at
+ * the same k. */
 
 /* The launch shape rdcnn_run(h, T, *variant, out->k) would use, without
  * running anything.  In: *variant (RDCNN_VARIANT_*, AUTO allowed) and

@@ -40,6 +40,7 @@ VARIANT_STEP1 = 1
 VARIANT_TEMPORAL = 2
 VARIANT_GENERIC = 3
 VARIANT_TEMPORAL2 = 4
+VARIANT_TEMPORAL_WIDE = 5
 
 PARAM_FIELDS = ("dt", "a", "b", "eps", "c", "Du", "Dv")
 STATIC_SCRATCH_BYTES = 16 << 20  # RDCNN_STATIC_SCRATCH_BYTES

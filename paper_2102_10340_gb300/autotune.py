@@ -13,7 +13,8 @@ _cache: dict = {}
 
 GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (0, 32, 64, 128, 256)] + \
                       [("temporal2", k, r) for k in (4, 6, 8) for r in (0, 64, 176, 256)] + \
-                      [("step1", 1, r) for r in (4, 8, 16)]
+                      [("temporal_wide", k, r) for k in (2, 3, 4) for r in (0, 32, 64, 128)] + \
+                      [("step1", 1, r) for r in (4, 8, 16, 32)]
 GRID_CANDIDATES_F64 = [("temporal", k, r) for k in (2, 3, 4) for r in (0, 32, 64, 128)] + \
                       [("temporal2", k, r) for k in (2, 4) for r in (0, 64)] + \
                       [("step1", 1, r) for r in (4, 8, 16)]
@@ -43,9 +44,12 @@ def tune_grid(grid, x=None, trial_steps: int = 48, force: bool = False) -> dict:
         best = {"variant": "generic", "k": 1, "rows": 0, "ms_per_step": None}
         _cache[key] = best
         return dict(best)
-    cands = GRID_CANDIDATES_F32 if grid.dtype == torch.float32 else GRID_CANDIDATES_F64
-    if getattr(grid, "boundary", "periodic") != "periodic" or grid.reaction == "cenn":
-        cands = [c for c in cands if c[0] != "temporal2"]  # periodic FHN / NONE only
+    cands = GRID_CANDIDATES_F64 if grid.dtype == torch.float64 else GRID_CANDIDATES_F32
+    if getattr(grid, "boundary", "periodic") != "periodic" or grid.reaction == "cenn" \
+            or grid.dtype in (torch.bfloat16, torch.float16):
+        cands = [c for c in cands if c[0] != "temporal2"]  # periodic FHN / NONE in FP32 / FP64 only
+    if grid.nm % 8 != 0:
+        cands = [c for c in cands if c[0] != "temporal_wide"]  # 8 values per lane
     T = 240 * max(1, trial_steps // 48)  # divisible by every candidate depth
     best = None
     for variant, k, rows in cands:

@@ -175,9 +175,17 @@ namespace rdk {
 // Resolve AUTO and the default depth for a run of h; vec_ok says whether the
 // vectorised variants may run (NM multiple of the vector width, aligned
 // buffers).  Returns RDCNN_OK or RDCNN_EINVAL.
-static int resolve_variant(const rdcnn_t *h, bool vec_ok, int *variant, int *k) {
-    if (*variant < RDCNN_VARIANT_AUTO || *variant > RDCNN_VARIANT_TEMPORAL2)
+static int resolve_variant(const rdcnn_t *h, bool vec_ok, bool wide_ok, int *variant, int *k) {
+    if (*variant < RDCNN_VARIANT_AUTO || *variant > RDCNN_VARIANT_TEMPORAL_WIDE)
         return set_error(RDCNN_EINVAL, "unknown variant %d", *variant);
+    if (*variant == RDCNN_VARIANT_TEMPORAL_WIDE) {
+        if (h->dtype == RDCNN_F64) return set_error(RDCNN_EINVAL, "RDCNN_VARIANT_TEMPORAL_WIDE has no FP64 form");
+        if (!wide_ok)
+            return set_error(RDCNN_EINVAL, "RDCNN_VARIANT_TEMPORAL_WIDE needs NM %% 8 == 0 and 16-byte aligned buffers");
+        if (*k == 0) *k = h->tune_k ? std::min(h->tune_k, kMaxKWide) : kMaxKWide;
+        if (*k < 1 || *k > kMaxKWide) return set_error(RDCNN_EINVAL, "k must be in 1..%d for the wide variant", kMaxKWide);
+        return RDCNN_OK;
+    }
     if (*variant == RDCNN_VARIANT_AUTO) *variant = vec_ok ? RDCNN_VARIANT_TEMPORAL : RDCNN_VARIANT_GENERIC;
     if ((*variant == RDCNN_VARIANT_STEP1 || *variant == RDCNN_VARIANT_TEMPORAL ||
          *variant == RDCNN_VARIANT_TEMPORAL2) && !vec_ok)
@@ -198,27 +206,30 @@ static int resolve_variant(const rdcnn_t *h, bool vec_ok, int *variant, int *k) 
     return RDCNN_OK;
 }
 
-static bool vec_ok_for(const rdcnn_t *h) {
-    const bool nm_ok = (h->nm % vec_width(h->dtype) == 0);
+// Whether the vectorised kernels may run on h's planes: NM a multiple of
+// `width` values and every plane aligned to `align` bytes.
+static bool planes_ok(const rdcnn_t *h, int width, size_t align) {
+    const bool nm_ok = (h->nm % width == 0);
     if (!h->bound) return nm_ok;
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
     const char *ws = (const char *)h->ws;
-    const size_t a = vec_align(h->dtype);
-    return nm_ok && aligned_to(h->u, a) && aligned_to(h->v, a) && aligned_to(ws, a) &&
-           aligned_to(ws + plane_stride(plane), a);
+    return nm_ok && aligned_to(h->u, align) && aligned_to(h->v, align) && aligned_to(ws, align) &&
+           aligned_to(ws + plane_stride(plane), align);
 }
+static bool vec_ok_for(const rdcnn_t *h) { return planes_ok(h, vec_width(h->dtype), vec_align(h->dtype)); }
+static bool wide_ok_for(const rdcnn_t *h) { return planes_ok(h, 8, 16); }
 
 int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
-    if (variant < RDCNN_VARIANT_AUTO || variant > RDCNN_VARIANT_TEMPORAL2)
+    if (variant < RDCNN_VARIANT_AUTO || variant > RDCNN_VARIANT_TEMPORAL_WIDE)
         return set_error(RDCNN_EINVAL, "unknown variant %d", variant);
     if (T == 0) return RDCNN_OK;
     const size_t plane = (size_t)h->nn * h->nm * elem_size(h->dtype);
     char *ws = (char *)h->ws;
     void *su = ws, *sv = ws + plane_stride(plane);
-    const int rv = resolve_variant(h, vec_ok_for(h), &variant, &k);
+    const int rv = resolve_variant(h, vec_ok_for(h), wide_ok_for(h), &variant, &k);
     if (rv < 0) return rv;
     const void *cu = h->u, *cv = h->v;
     void *nu = su, *nv = sv;
@@ -228,7 +239,10 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
         const int64_t done = T - left;
         if (every > 0) kk = (int)std::min<int64_t>(kk, every - done % every);
         cudaError_t e;
-        if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
+        if (variant == RDCNN_VARIANT_TEMPORAL_WIDE)
+            e = launch_temporal_wide(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm,
+                                     h->p, h->tune_rows, h->stream);  // 0 = chosen by the launcher
+        else if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
             e = launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
                                       h->tune_rows, h->stream);  // 0 = chosen by the launcher
         else if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
@@ -268,7 +282,7 @@ int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k) { return run_core(h, T,
 int rdcnn_plan(const rdcnn_t *h, int *variant, rdcnn_tune *out) {
     if (!h || !variant || !out) return set_error(RDCNN_EINVAL, "NULL argument");
     int v = *variant, k = out->k;
-    const int rv = resolve_variant(h, vec_ok_for(h), &v, &k);
+    const int rv = resolve_variant(h, vec_ok_for(h), wide_ok_for(h), &v, &k);
     if (rv < 0) return rv;
     const int rows = v == RDCNN_VARIANT_GENERIC ? 0 : h->tune_rows;
     out->rows = plan_rows(h->dtype, h->reaction, h->boundary, v, k, h->nn, h->nm, rows);

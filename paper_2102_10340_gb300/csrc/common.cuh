@@ -86,27 +86,31 @@ template <> struct LaneVec<double, 2> { typedef double2 type; };
 template <> struct LaneVec<__nv_bfloat16, 4> { typedef uint2 type; };
 template <> struct LaneVec<__half, 4> { typedef uint2 type; };
 
-// A 16-bit storage type read 8 values (16 bytes) per lane: the same bits in
-// memory as E, a distinct type so that a pipeline instantiated on it takes
-// the wider lane (the depth-1 pipeline of 16-bit planes, where the fixed
-// per-row costs of a lane then cover twice the cells).
-template <typename E> struct Wide16 { E x; };
-template <typename E> struct LaneVec<Wide16<E>, 8> { typedef uint4 type; };
+// A storage type E read 8 values per lane (16 bytes of a 16-bit type, 32 of
+// float): the same bits in memory as E, a distinct type so that a pipeline
+// instantiated on it takes the wider lane.  The fixed per-row costs of a
+// lane (ring copies, addresses, shuffles, loop) then cover twice the cells,
+// and one halo lane covers a depth of up to 8 instead of 4.
+template <typename E> struct Wide { E x; };
+struct __align__(16) Float8 { float4 a, b; };
+template <> struct LaneVec<Wide<__nv_bfloat16>, 8> { typedef uint4 type; };
+template <> struct LaneVec<Wide<__half>, 8> { typedef uint4 type; };
+template <> struct LaneVec<Wide<float>, 8> { typedef Float8 type; };
 
-// The 16-bit format behind a storage type (itself for the plain types).
+// The element format behind a storage type (itself for the plain types).
 template <typename T> struct Base16 { typedef T type; };
-template <typename E> struct Base16<Wide16<E>> { typedef E type; };
+template <typename E> struct Base16<Wide<E>> { typedef E type; };
 
 // Lane width of the register pipelines: 4 values (2 doubles) of every
 // storage type, so that 16-bit planes share the FP32 lane layout and
-// register budget (8 bytes per lane and field); 8 for Wide16.
+// register budget (8 bytes per lane and field); 8 for Wide.
 template <typename T> struct Vec {
     static constexpr int N = std::is_same<T, double>::value ? 2 : 4;
     typedef typename LaneVec<T, N>::type type;
 };
-template <typename E> struct Vec<Wide16<E>> {
+template <typename E> struct Vec<Wide<E>> {
     static constexpr int N = 8;
-    typedef uint4 type;
+    typedef typename LaneVec<Wide<E>, 8>::type type;
 };
 
 // Arithmetic type of a storage type: 16-bit planes are computed in FP32 and
@@ -114,7 +118,7 @@ template <typename E> struct Vec<Wide16<E>> {
 template <typename T> struct Compute { typedef T type; };
 template <> struct Compute<__nv_bfloat16> { typedef float type; };
 template <> struct Compute<__half> { typedef float type; };
-template <typename E> struct Compute<Wide16<E>> { typedef float type; };
+template <typename E> struct Compute<Wide<E>> { typedef float type; };
 template <typename T> using CT = typename Compute<T>::type;
 
 // float / double planes: arithmetic in the storage type itself.
@@ -126,6 +130,9 @@ template <typename T, int V>
 __device__ __forceinline__ void unpack_vec(const typename LaneVec<T, V>::type &x, CT<T> (&d)[V]) {
     if constexpr (std::is_same<T, float>::value) {
         d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+    } else if constexpr (std::is_same<T, Wide<float>>::value) {
+        d[0] = x.a.x; d[1] = x.a.y; d[2] = x.a.z; d[3] = x.a.w;
+        d[4] = x.b.x; d[5] = x.b.y; d[6] = x.b.z; d[7] = x.b.w;
     } else if constexpr (std::is_same<T, double>::value) {
         d[0] = x.x; d[1] = x.y;
     } else {
@@ -146,6 +153,11 @@ template <typename T, int V>
 __device__ __forceinline__ typename LaneVec<T, V>::type pack_vec(const CT<T> (&s)[V]) {
     if constexpr (std::is_same<T, float>::value) {
         return make_float4(s[0], s[1], s[2], s[3]);
+    } else if constexpr (std::is_same<T, Wide<float>>::value) {
+        Float8 r;
+        r.a = make_float4(s[0], s[1], s[2], s[3]);
+        r.b = make_float4(s[4], s[5], s[6], s[7]);
+        return r;
     } else if constexpr (std::is_same<T, double>::value) {
         return make_double2(s[0], s[1]);
     } else {

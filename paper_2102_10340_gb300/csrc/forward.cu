@@ -176,7 +176,7 @@ cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, vo
         // (same arithmetic, one rounding per step: the same bits), with 8 values
         // (16 bytes) per lane when NM and the alignment allow.
         if (nm % 8 == 0 && aligned16(u) && aligned16(v) && aligned16(un) && aligned16(vn))
-            return temporal_launch<Wide16<T>, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+            return temporal_launch<Wide<T>, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
         return temporal_launch<T, 1>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
     } else {
         constexpr int V = Vec<T>::N;
@@ -319,6 +319,22 @@ cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const 
     });
 }
 
+cudaError_t launch_temporal_wide(int dtype, int reaction, int boundary, int k, const void *u,
+                                 const void *v, void *un, void *vn, int64_t nn, int64_t nm,
+                                 const rdcnn_params &p, int rows, cudaStream_t s) {
+    if (dtype == RDCNN_F64) return cudaErrorInvalidValue;
+    return with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        return with_depth(k, [&](auto kk) -> cudaError_t {
+            constexpr int K = decltype(kk)::value;
+            if constexpr (K <= kMaxKWide && !std::is_same<T, double>::value)
+                return temporal_launch<Wide<T>, K>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
+            else
+                return cudaErrorInvalidValue;
+        });
+    });
+}
+
 // FP32 / FP64 storage, periodic FitzHugh-Nagumo / pure diffusion only (the caller checks).
 cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
@@ -371,6 +387,12 @@ int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t
                 if constexpr (K >= 2 && is_f32_f64<T>()) {
                     if (variant == RDCNN_VARIANT_TEMPORAL2) {
                         out = split_rows<T, K>(reaction, nn, nm, rows);
+                        return cudaSuccess;
+                    }
+                }
+                if constexpr (K <= kMaxKWide && !std::is_same<T, double>::value) {
+                    if (variant == RDCNN_VARIANT_TEMPORAL_WIDE) {
+                        out = temporal_rows<Wide<T>, K>(reaction, boundary, nn, nm, rows);
                         return cudaSuccess;
                     }
                 }

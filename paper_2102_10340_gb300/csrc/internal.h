@@ -27,6 +27,7 @@ namespace rdk {
 // Launch-shape limits of the vectorised kernels.
 constexpr int kMaxK32 = 8;  // temporal depth, FP32
 constexpr int kMaxK64 = 4;  // temporal depth, FP64
+constexpr int kMaxKWide = 4;  // temporal depth with 8 values per lane
 
 inline int vec_width(int dtype) { return dtype == RDCNN_F64 ? 2 : 4; }
 inline size_t elem_size(int dtype) {
@@ -85,6 +86,11 @@ cudaError_t launch_step1(int dtype, int reaction, int boundary, const void *u, c
 cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const void *u,
                             const void *v, void *un, void *vn, int64_t nn, int64_t nm,
                             const rdcnn_params &p, int rows, cudaStream_t s);
+// The temporal pipeline with 8 values per lane (k = 1..4; F32, BF16, F16;
+// NM % 8 == 0 and 16-byte aligned planes, which the caller checks).
+cudaError_t launch_temporal_wide(int dtype, int reaction, int boundary, int k, const void *u,
+                                 const void *v, void *un, void *vn, int64_t nn, int64_t nm,
+                                 const rdcnn_params &p, int rows, cudaStream_t s);
 // The temporal pipeline with the K stages split across a warp pair (k >= 2);
 // periodic boundary, FitzHugh-Nagumo or no reaction.
 cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,

@@ -58,7 +58,14 @@ __device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, in
                                            const T *__restrict__ u, const T *__restrict__ v) {
     const int lane = threadIdx.x & 31;
     const int64_t off = (int64_t)g * nm + lc;
-    if constexpr (sizeof(typename Vec<T>::type) == 16) {
+    if constexpr (sizeof(typename Vec<T>::type) == 32) {  // two 16-byte halves per field
+        char *su = reinterpret_cast<char *>(&r.slot[m % kRing][0][lane]);
+        char *sv = reinterpret_cast<char *>(&r.slot[m % kRing][1][lane]);
+        cp_async16(su, u + off);
+        cp_async16(su + 16, reinterpret_cast<const char *>(u + off) + 16);
+        cp_async16(sv, v + off);
+        cp_async16(sv + 16, reinterpret_cast<const char *>(v + off) + 16);
+    } else if constexpr (sizeof(typename Vec<T>::type) == 16) {
         cp_async16(&r.slot[m % kRing][0][lane], u + off);
         cp_async16(&r.slot[m % kRing][1][lane], v + off);
     } else {

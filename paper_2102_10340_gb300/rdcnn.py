@@ -24,7 +24,8 @@ DEFAULT_PARAMS = {"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0
 GRAD_NAMES = ("Du", "Dv", "a", "b", "eps", "c")
 
 _VARIANTS = {"auto": L.VARIANT_AUTO, "step1": L.VARIANT_STEP1, "temporal": L.VARIANT_TEMPORAL,
-             "generic": L.VARIANT_GENERIC, "temporal2": L.VARIANT_TEMPORAL2}
+             "generic": L.VARIANT_GENERIC, "temporal2": L.VARIANT_TEMPORAL2,
+             "temporal_wide": L.VARIANT_TEMPORAL_WIDE}
 _REACTIONS = {"fhn": L.REACTION_FHN, "none": L.REACTION_NONE, "cenn": L.REACTION_CENN}
 _BOUNDARIES = {"periodic": L.BC_PERIODIC, "zeroflux": L.BC_ZEROFLUX}
 

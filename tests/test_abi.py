@@ -175,7 +175,7 @@ def test_binding_constants_match_header(L):
     enums = header_enums()
     for name in ("BC_PERIODIC", "BC_ZEROFLUX", "F32", "F64", "BF16", "F16", "REACTION_FHN", "REACTION_NONE",
                  "REACTION_CENN", "VARIANT_AUTO", "VARIANT_STEP1", "VARIANT_TEMPORAL",
-                 "VARIANT_GENERIC", "VARIANT_TEMPORAL2"):
+                 "VARIANT_GENERIC", "VARIANT_TEMPORAL2", "VARIANT_TEMPORAL_WIDE"):
         assert getattr(L, name) == enums[name], name
 
 

@@ -28,6 +28,8 @@ def _variants(nm, dtype):
         out += [("step1", 0), ("temporal", 1), ("temporal", 2)]
         out += [("temporal", k) for k in ((3, 4, 5, 8) if dtype == F32 else (3, 4))]
         out += [("temporal2", k) for k in ((2, 5, 8) if dtype == F32 else (2, 4))]
+    if dtype == F32 and nm % 8 == 0:
+        out += [("temporal_wide", k) for k in (1, 2, 4)]
     return out
 
 
@@ -73,7 +75,8 @@ def test_ragged_and_tiny_grids(rd, oracle_mod, shape, dtype):
 def test_launch_shape_does_not_change_bits(rd, rows):
     x = f32(inp.uniform_field(9, 70, 136))
     base = gpu_run(rd, x, -x, inp.default_params(), 23, F32, "generic")
-    for variant, k in (("step1", 0), ("temporal", 3), ("temporal", 8), ("temporal2", 3), ("temporal2", 8)):
+    for variant, k in (("step1", 0), ("temporal", 3), ("temporal", 8), ("temporal2", 3), ("temporal2", 8),
+                       ("temporal_wide", 3), ("temporal_wide", 4)):
         got = gpu_run(rd, x, -x, inp.default_params(), 23, F32, variant, k, rows=rows)
         assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1]), (variant, k, rows)
 
@@ -221,3 +224,17 @@ def test_launch_counter_counts(rd):
     before = rd.launch_count()
     gpu_run(rd, np.zeros((8, 8)), np.zeros((8, 8)), inp.default_params(), 12, F32, "temporal", 4)
     assert rd.launch_count() - before >= 3
+
+
+def test_wide_variant_rejects_unsupported_planes(rd):
+    g = rd.Grid(16, 20, None, dtype=F32)  # NM = 20: not a multiple of 8
+    g.set_state(torch.zeros((16, 20), device="cuda"), torch.zeros((16, 20), device="cuda"))
+    with pytest.raises(rd.RDCNNError):
+        g.run(4, variant="temporal_wide", k=2)
+    g.run(4, variant="temporal", k=2)  # the 4-value lane still runs
+    g.close()
+    g = rd.Grid(16, 16, None, dtype=F64)
+    g.set_state(torch.zeros((16, 16), device="cuda", dtype=F64), torch.zeros((16, 16), device="cuda", dtype=F64))
+    with pytest.raises(rd.RDCNNError):
+        g.run(4, variant="temporal_wide", k=2)
+    g.close()

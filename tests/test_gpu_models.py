@@ -44,6 +44,8 @@ def _variants(nm, dtype):
     out = [("generic", 0)]
     if nm % vec == 0:
         out += [("step1", 0)] + [("temporal", k) for k in ((1, 2, 3, 5, 8) if dtype == F32 else (1, 2, 3, 4))]
+    if dtype == F32 and nm % 8 == 0:
+        out += [("temporal_wide", 2), ("temporal_wide", 4)]
     return out
 
 

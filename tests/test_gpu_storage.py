@@ -117,3 +117,15 @@ def test_storage_full_size_windows(rd, oracle_mod, storage, dt):
         su, sv = oracle_mod.run_storage(x[win], x[win], inp.default_params(), T, 1, storage)
         core = (slice(T, W - T), slice(T, W - T))
         assert normwise(gu[win][core], su[core]) <= 5e-4 and normwise(gv[win][core], sv[core]) <= 5e-4
+
+
+@pytest.mark.parametrize("storage,dt", STORAGE, ids=[s for s, _ in STORAGE])
+def test_storage_wide_lanes_same_bits(rd, oracle_mod, storage, dt):
+    """8 values per lane (RDCNN_VARIANT_TEMPORAL_WIDE) against 4 at the same depth: same bits."""
+    x = oracle_mod.round_to_storage(inp.uniform_field(95, 70, 264), storage).astype(np.float64)
+    for k in (1, 3, 4):
+        a = gpu_run(rd, x, x, inp.default_params(), 2 * k + 1, dt, "temporal", k)
+        b = gpu_run(rd, x, x, inp.default_params(), 2 * k + 1, dt, "temporal_wide", k)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), k
+    su, sv = oracle_mod.run_storage(x, x, inp.default_params(), 9, 4, storage)
+    _close(b[0], b[1], su, sv, storage, "wide k=4")
