@@ -73,6 +73,7 @@ __device__ __forceinline__ T warp_sum_t(T x) {
 // FP64 once per warp (FP64 arithmetic is slow here).
 template <typename T, int K, int RX>
 struct ReversePolicy {
+    static constexpr bool kLightCone = false;  // its stages also keep per-stage state rings in step
     typedef typename Vec<T>::type VT;
     const AdjCoef<T> &p;
     const StripGeom &geo;

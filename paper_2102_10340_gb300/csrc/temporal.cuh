@@ -141,7 +141,14 @@ template <int BC> struct RowWalk {
 //        stage s maps rows q-1 (A), q (B), q+1 (C) of its input to row q of
 //        its output (q = input-row index within the strip, see temporal_strip)
 //   P::finish(q, out)                    the row q leaving the last stage
-template <typename T, int K, int PH, int BC, class P>
+//
+// ACTIVE < K (the first 2K beats of a strip with a policy that allows it):
+// only stages s < ACTIVE compute; stage ACTIVE just keeps its input row for
+// the next beats.  Row q of the last stage needs stage s's rows from
+// q - (K - 1 - s) on, and the stored rows have q >= K, so stage s's rows
+// 0 .. s feed nothing that is stored.  Beat m computes stage s's row
+// m - s - 1, so stage s first matters at beat 2s + 2: ACTIVE = m / 2.
+template <typename T, int K, int PH, int BC, int ACTIVE = K, class P>
 __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec<T>::N> (&W)[3][K],
                                               const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
                                               int lc, bool rev, const T *__restrict__ u,
@@ -162,18 +169,33 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec
     pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        Slice<CT<T>, Vec<T>::N> &A = W[PH][s];
-        Slice<CT<T>, Vec<T>::N> &B = W[(PH + 1) % 3][s];
-        const CT<T> wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
-        const CT<T> eu = __shfl_down_sync(kFull, B.u[0], 1);
-        const CT<T> wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
-        const CT<T> ev = __shfl_down_sync(kFull, B.v[0], 1);
-        Slice<CT<T>, Vec<T>::N> out;
-        pol.stage(s, A, B, cur, wu, eu, wv, ev, m - s - 1, out);
-        W[(PH + 2) % 3][s] = cur;
-        cur = out;
+        if (s < ACTIVE) {
+            Slice<CT<T>, Vec<T>::N> &A = W[PH][s];
+            Slice<CT<T>, Vec<T>::N> &B = W[(PH + 1) % 3][s];
+            const CT<T> wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
+            const CT<T> eu = __shfl_down_sync(kFull, B.u[0], 1);
+            const CT<T> wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
+            const CT<T> ev = __shfl_down_sync(kFull, B.v[0], 1);
+            Slice<CT<T>, Vec<T>::N> out;
+            pol.stage(s, A, B, cur, wu, eu, wv, ev, m - s - 1, out);
+            W[(PH + 2) % 3][s] = cur;
+            cur = out;
+        } else if (s == ACTIVE) {
+            W[(PH + 2) % 3][s] = cur;  // stage s - 1's row, needed from the next beat on
+        }
     }
-    pol.finish(m - K, cur);
+    if constexpr (ACTIVE == K) pol.finish(m - K, cur);
+}
+
+// The first 2K beats of a strip (ACTIVE = M / 2), unrolled at compile time.
+template <typename T, int K, int BC, int M, class P>
+__device__ __forceinline__ void pipeline_fill(int total, Slice<CT<T>, Vec<T>::N> (&W)[3][K],
+                                              const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
+                                              int lc, bool rev, const T *__restrict__ u,
+                                              const T *__restrict__ v, P &pol) {
+    pipeline_beat<T, K, M % 3, BC, (M / 2 < K ? M / 2 : K)>(M, total, W, ring, walk, nn, nm, lc, rev, u, v, pol);
+    if constexpr (M + 1 < 2 * K)
+        pipeline_fill<T, K, BC, M + 1>(total, W, ring, walk, nn, nm, lc, rev, u, v, pol);
 }
 
 // Geometry of one (band, strip) work item for depth K and halo H.
@@ -242,17 +264,24 @@ __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__
         }
         cp_async_commit();
     }
-    for (int m = 0; m < geo.total; m += 3) {
-        pipeline_beat<T, K, 0>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
-        pipeline_beat<T, K, 1>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
-        pipeline_beat<T, K, 2>(m + 2, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+    // a strip has total = nout + 2K > 2K beats, so the fill always completes
+    constexpr int M0 = P::kLightCone ? 2 * K : 0;
+    if constexpr (P::kLightCone)
+        pipeline_fill<T, K, BC, 0>(geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+    for (int m = M0; m < geo.total; m += 3) {
+        pipeline_beat<T, K, M0 % 3>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+        pipeline_beat<T, K, (M0 + 1) % 3>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+        pipeline_beat<T, K, (M0 + 2) % 3>(m + 2, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
     }
     cp_async_wait<0>();
 }
 
 // Forward policy: Eq. 1 at every stage; the last stage's owned rows are stored.
+// Only owned rows are stored, so the fill may skip the stages outside their
+// light cone (kLightCone).
 template <typename T, int K, int RX>
 struct ForwardPolicy {
+    static constexpr bool kLightCone = true;
     const Coef<CT<T>> &p;
     const StripGeom &geo;
     T *__restrict__ un;
@@ -285,6 +314,7 @@ template <typename T> struct StagePlanes {
 // needs, K per launch.
 template <typename T, int K, int RX>
 struct ForwardAllPolicy {
+    static constexpr bool kLightCone = true;  // stores owned rows only (q >= K)
     const Coef<CT<T>> &p;
     const StripGeom &geo;
     const StagePlanes<T> &planes;
