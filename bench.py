@@ -339,7 +339,7 @@ def measure_storage_error(rd, torch, N=512, quick=False):
     return {"grid": [N, N], "init": "x ~ U[-1,1] seed 0, u = v = x", "reference": "FP64 kernels", "runs": out}
 
 
-def measure_batched(rd, torch, T=5000, quick=False):
+def measure_batched(rd, torch, T=5000, quick=False, tune=None):
     specs = inp.sweep_instances(0)
     if quick:
         specs = specs[:32]
@@ -352,7 +352,8 @@ def measure_batched(rd, torch, T=5000, quick=False):
         b.set_state(i, x, x)
     from paper_2102_10340_gb300 import autotune
 
-    tune = autotune.tune_batch(b, trial_steps=40 if not quick else 8)
+    if tune is None:
+        tune = autotune.tune_batch(b, trial_steps=40 if not quick else 8)
     b.set_tune(**tune)
     for i, x in enumerate(xs):
         b.set_state(i, x, x)
@@ -612,7 +613,8 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="small batched/adjoint/cpu legs")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
-    ap.add_argument("--no-tune", action="store_true", help="use --variant/--k/--rows instead of autotuning")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use --variant/--k/--rows instead of autotuning (with --leg batched: --k/--rows)")
     ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage"), default=None,
                     help="run only this follow-on measurement (small, for profiling) and print it")
     ap.add_argument("--variant", default="temporal",
@@ -629,7 +631,8 @@ def main(argv=None):
 
         from paper_2102_10340_gb300 import rdcnn as rd
 
-        fn = {"batched": lambda: measure_batched(rd, torch, quick=True),
+        btune = {"k": args.k, "rows": args.rows} if args.no_tune else None
+        fn = {"batched": lambda: measure_batched(rd, torch, quick=True, tune=btune),
               "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
               "search": lambda: measure_search(torch, quick=True),
               "models": lambda: measure_models(rd, torch),
