@@ -73,7 +73,10 @@ __device__ __forceinline__ T warp_sum_t(T x) {
 // FP64 once per warp (FP64 arithmetic is slow here).
 template <typename T, int K, int RX>
 struct ReversePolicy {
-    static constexpr bool kLightCone = false;  // its stages also keep per-stage state rings in step
+    // A stage reads only its own ring slot of the beat and sums over owned
+    // rows (q >= K, inside the light cone), so the fill may skip stages; the
+    // state-row copies are issued per beat for every stage regardless.
+    static constexpr bool kLightCone = true;
     typedef typename Vec<T>::type VT;
     const AdjCoef<T> &p;
     const StripGeom &geo;
