@@ -206,8 +206,9 @@ cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, vo
 int auto_rows_temporal(int K, int64_t nn, int64_t nm, int bands, int blocks_per_sm,
                        int warps_per_block) {
     const int64_t cells = nn * nm;
-    if (cells < (int64_t(1) << 17)) return 4;
-    if (cells < (int64_t(1) << 19)) return 8;
+    // size classes from a sweep at 256^2 .. 2048^2 (with the light-cone fill):
+    // 512^2, k = 6: 4 rows 150 Gcell/s, 8 rows 127
+    if (cells < (int64_t(1) << 19)) return 4;
     if (cells < (int64_t(1) << 22)) return 16;
     const int64_t cap = (int64_t)sm_count() * std::max(1, blocks_per_sm) * warps_per_block;
     static const int cand[] = {32, 48, 64, 96, 128, 160, 192, 256};
