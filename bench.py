@@ -190,9 +190,21 @@ def oracle_sample(target_s: float = 12.0, n=N_GRID):
     oracle.run(u, v, params, steps, nthreads=threads)
     dt = time.perf_counter() - t0
     rate = n * n * steps / dt / 1e9
+    # the same oracle at 1024^2, one thread and all threads (short samples, ~1.5 s each)
+    detail = {}
+    xs = np.asarray(inp.smooth_noise(0, 1024, 1024), dtype=np.float32).astype(np.float64)
+    for name, nt in (("single_thread_1024", 1), ("all_threads_1024", threads)):
+        su, sv = oracle.run(xs, xs, params, 1, nthreads=nt)
+        t0 = time.perf_counter()
+        oracle.run(su, sv, params, 2, nthreads=nt)
+        per = (time.perf_counter() - t0) / 2
+        k = int(max(1, min(500, 1.5 / max(per, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.run(su, sv, params, k, nthreads=nt)
+        detail[name] = {"value": 1024 * 1024 * k / (time.perf_counter() - t0) / 1e9, "steps": k, "threads": nt}
     return {"value": rate, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} FP64 steps of the {n}x{n} headline grid (OpenMP rows, {threads} threads), "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s", "detail": detail}
 
 
 def run_reference(args):
@@ -337,6 +349,32 @@ def measure_storage_error(rd, torch, N=512, quick=False):
                          "edge_frac": edge, "edge_frac_ref": ref_edge}
         out[f"T={T}"] = row
     return {"grid": [N, N], "init": "x ~ U[-1,1] seed 0, u = v = x", "reference": "FP64 kernels", "runs": out}
+
+
+def measure_image(rd, torch, N=1024, T=10000, quick=False):
+    """Image-processing mode: N x N FP32 smooth-noise image (periodic Gaussian blur, sigma = 8,
+    of U[0, 1] seed 0, rescaled to [-1, 1]), u = v = x, default gene, T steps.  The four planes
+    (16 MiB at 1024^2) stay in L2, so this is an L2-resident number, not an HBM one."""
+    from paper_2102_10340_gb300 import autotune
+
+    if quick:
+        T = 1000
+    x = torch.from_numpy(np.asarray(inp.smooth_noise(0, N, N), dtype=np.float32)).cuda()
+    g = rd.Grid(N, N, inp.default_params(), dtype=torch.float32)
+    tune = autotune.tune_grid(g, x)
+    g.init(x, 1.0).run(64, variant=tune["variant"], k=tune["k"])
+    g.init(x, 1.0)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    g.run(T, variant=tune["variant"], k=tune["k"])
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e)
+    g.close()
+    return {"grid": [N, N], "T": T, "value": N * N * T / (ms * 1e-3) / 1e9, "unit": "Gcell-updates/s",
+            "ms": ms, "tune": {k: tune[k] for k in ("variant", "k", "rows")},
+            "note": "state + ping-pong = 16 MiB, L2-resident (126 MiB L2)"}
 
 
 def measure_batched(rd, torch, T=5000, quick=False, tune=None):
@@ -575,6 +613,7 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extras:
+        extra["image"] = measure_image(rd, torch, quick=args.quick)
         extra["snapshots"] = measure_snapshots(rd, grid, x_dev, torch, T=200 if args.quick else 2000,
                                                every=20 if args.quick else 200)
         extra["batched"] = measure_batched(rd, torch, quick=args.quick)
@@ -615,7 +654,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="use --variant/--k/--rows instead of autotuning (with --leg batched: --k/--rows)")
-    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage"), default=None,
+    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage", "image"), default=None,
                     help="run only this follow-on measurement (small, for profiling) and print it")
     ap.add_argument("--variant", default="temporal",
                     choices=("temporal", "temporal2", "temporal_wide", "step1", "generic"))
@@ -636,7 +675,8 @@ def main(argv=None):
               "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
               "search": lambda: measure_search(torch, quick=True),
               "models": lambda: measure_models(rd, torch),
-              "storage": lambda: measure_storage(rd, torch)}[args.leg]
+              "storage": lambda: measure_storage(rd, torch),
+              "image": lambda: measure_image(rd, torch)}[args.leg]
         print(json.dumps({"leg": args.leg, **fn()}), flush=True)
         return 0
     return run_ours(args)
