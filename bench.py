@@ -149,6 +149,18 @@ def profiled_traffic(kernel_md: str, k: int, rows: int):
     return float(t.group(1)) * 1e6, f"profiles/{kernel_md}"
 
 
+def profiled_instructions(kernel_md: str):
+    """Warp instructions per launch from the same committed summary (None if absent)."""
+    import re
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", kernel_md)).read()
+    except OSError:
+        return None
+    m = re.search(r"warp instructions per launch:\s*([0-9.]+)\s*M", text)
+    return float(m.group(1)) * 1e6 if m else None
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -590,7 +602,16 @@ def run_ours(args):
                  "temporal_wide": "k_temporal_wide"}[variant]
         traffic, tsrc = (profiled_traffic(f"{kname}_f32_k{k}_4096.md", k, plan["rows"]) if N == 4096
                          else (None, "other grid"))
+        issue = None
+        inst = profiled_instructions(f"{kname}_f32_k{k}_4096.md") if traffic is not None else None
+        if inst:
+            # warp-instruction issue: 4 schedulers per SM, one instruction per clock each
+            peak_issue = 152 * 4 * peaks["sm_max_mhz"] * 1e6
+            issue = {"achieved": inst / (launch_ms * 1e-3), "peak": peak_issue, "unit": "warp-inst/s",
+                     "frac": inst / (launch_ms * 1e-3) / peak_issue, "instructions_per_launch": inst,
+                     "source": tsrc}
         roofline = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
+                    "issue": issue,
                     "traffic": traffic, "traffic_source": tsrc,
                     "algorithmic_bytes": BYTES_PER_CELL_STEP * cells, "kernel": f"{kname}<float,K={k}>",
                     "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz "
