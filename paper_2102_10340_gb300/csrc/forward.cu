@@ -35,7 +35,7 @@ namespace rdk {
 
 namespace {
 
-constexpr int kStep1Block = 256;
+constexpr int kStep1Block = 128;  // 72 registers: 7 blocks = 28 warps per SM (256: 24 warps, -2.5 %)
 
 // --------------------------------------------------------------------------- single step
 
