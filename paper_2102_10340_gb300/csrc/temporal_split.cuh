@@ -14,6 +14,13 @@
 // (a pair without work) happens before any barrier and for both warps.
 //
 // Same arithmetic and the same cells as temporal_strip: identical bits.
+//
+// Light-cone fill (as in temporal.cuh): global stage s first matters at the
+// equivalent single-warp beat 2s + 2.  The producer's beat m is that beat;
+// the consumer's beat m is beat m - 1.  The first beats of both warps are
+// unrolled with compile-time counts of computing stages (ACT); the stage
+// just past them only keeps its input row.  Every beat still ends with the
+// pair barrier, so the two warps' barrier counts stay equal.
 #pragma once
 
 #include "temporal.cuh"
@@ -40,7 +47,7 @@ __device__ __forceinline__ void hand_read(const Handoff<T> &h, int k, Slice<T> &
 
 // Producer beat: input row m from the ring through stages 1 .. K1; the stage-K1
 // row (input-row index m - K1) goes to handoff slot m % 2.
-template <typename T, int K1, int RX, int PH>
+template <typename T, int K1, int RX, int PH, int ACT = K1>
 __device__ __forceinline__ void split_producer_beat(int m, int total, Slice<T> (&W)[3][K1],
                                                     const RowRing<T> &ring, const Handoff<T> &hand,
                                                     int &g_issue, int nn, int nm, int lc,
@@ -61,16 +68,20 @@ __device__ __forceinline__ void split_producer_beat(int m, int total, Slice<T> (
         ring_read(ring, m, cur);
 #pragma unroll
         for (int s = 0; s < K1; ++s) {
-            Slice<T> &A = W[PH][s];
-            Slice<T> &B = W[(PH + 1) % 3][s];
-            const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
-            const T eu = __shfl_down_sync(kFull, B.u[0], 1);
-            const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
-            const T ev = __shfl_down_sync(kFull, B.v[0], 1);
-            Slice<T> out;
-            slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
-            W[(PH + 2) % 3][s] = cur;
-            cur = out;
+            if (s < ACT) {
+                Slice<T> &A = W[PH][s];
+                Slice<T> &B = W[(PH + 1) % 3][s];
+                const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
+                const T eu = __shfl_down_sync(kFull, B.u[0], 1);
+                const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
+                const T ev = __shfl_down_sync(kFull, B.v[0], 1);
+                Slice<T> out;
+                slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
+                W[(PH + 2) % 3][s] = cur;
+                cur = out;
+            } else if (s == ACT) {
+                W[(PH + 2) % 3][s] = cur;
+            }
         }
         VT a, b;
         if constexpr (V == 4) {
@@ -88,7 +99,7 @@ __device__ __forceinline__ void split_producer_beat(int m, int total, Slice<T> (
 
 // Consumer beat: the producer's row of beat m - 1 through stages K1+1 .. K; the
 // final row (input-row index m - 1 - K) is stored when the strip owns it.
-template <typename T, int K, int K2, int RX, int PH>
+template <typename T, int K, int K2, int RX, int PH, int ACT = K2, bool KEEP = false>
 __device__ __forceinline__ void split_consumer_beat(int m, int total, Slice<T> (&W)[3][K2],
                                                     const Handoff<T> &hand, const StripGeom &geo,
                                                     T *__restrict__ un, T *__restrict__ vn, int nm,
@@ -100,18 +111,22 @@ __device__ __forceinline__ void split_consumer_beat(int m, int total, Slice<T> (
         hand_read(hand, (m - 1) % 2, cur);
 #pragma unroll
         for (int s = 0; s < K2; ++s) {
-            Slice<T> &A = W[PH][s];
-            Slice<T> &B = W[(PH + 1) % 3][s];
-            const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
-            const T eu = __shfl_down_sync(kFull, B.u[0], 1);
-            const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
-            const T ev = __shfl_down_sync(kFull, B.v[0], 1);
-            Slice<T> out;
-            slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
-            W[(PH + 2) % 3][s] = cur;
-            cur = out;
+            if (s < ACT) {
+                Slice<T> &A = W[PH][s];
+                Slice<T> &B = W[(PH + 1) % 3][s];
+                const T wu = __shfl_up_sync(kFull, B.u[V - 1], 1);
+                const T eu = __shfl_down_sync(kFull, B.u[0], 1);
+                const T wv = __shfl_up_sync(kFull, B.v[V - 1], 1);
+                const T ev = __shfl_down_sync(kFull, B.v[0], 1);
+                Slice<T> out;
+                slice_update<T, RX>(A, B, cur, wu, eu, wv, ev, p, out);
+                W[(PH + 2) % 3][s] = cur;
+                cur = out;
+            } else if (KEEP && s == ACT) {
+                W[(PH + 2) % 3][s] = cur;
+            }
         }
-        const int orow = m - 1 - 2 * K;
+        const int orow = m - 1 - 2 * K;  // negative throughout the fill
         if (orow >= 0 && geo.st_lane) {
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
             store_vec<T>(un + off, cur.u);
@@ -119,6 +134,33 @@ __device__ __forceinline__ void split_consumer_beat(int m, int total, Slice<T> (
         }
     }
     pair_barrier(bar_id);
+}
+
+// Fill beats 0 .. F-1 of the producer: ACT = min(M / 2, K1).
+template <typename T, int K1, int RX, int M, int F>
+__device__ __forceinline__ void split_producer_fill(int total, Slice<T> (&W)[3][K1], const RowRing<T> &ring,
+                                                    const Handoff<T> &hand, int &g_issue, int nn, int nm,
+                                                    int lc, const T *__restrict__ u, const T *__restrict__ v,
+                                                    int bar_id, const Coef<T> &p) {
+    split_producer_beat<T, K1, RX, M % 3, (M / 2 < K1 ? M / 2 : K1)>(M, total, W, ring, hand, g_issue, nn, nm,
+                                                                     lc, u, v, bar_id, p);
+    if constexpr (M + 1 < F)
+        split_producer_fill<T, K1, RX, M + 1, F>(total, W, ring, hand, g_issue, nn, nm, lc, u, v, bar_id, p);
+}
+
+// Fill beats 0 .. F-1 of the consumer (equivalent beat M - 1): local stage j
+// computes when M - 1 >= 2 (K1 + j) + 2; the next one keeps its input once
+// the handoff row is valid (M - 1 >= 2 K1).
+template <typename T, int K, int K2, int RX, int M, int F>
+__device__ __forceinline__ void split_consumer_fill(int total, Slice<T> (&W)[3][K2], const Handoff<T> &hand,
+                                                    const StripGeom &geo, T *__restrict__ un,
+                                                    T *__restrict__ vn, int nm, int bar_id, const Coef<T> &p) {
+    constexpr int K1 = K - K2;
+    constexpr int D = (M >= 1 ? (M - 1) / 2 : -1) - K1;  // computing stages, before clamping
+    constexpr int ACT = D < 0 ? 0 : (D > K2 ? K2 : D);
+    split_consumer_beat<T, K, K2, RX, M % 3, ACT, (D >= 0)>(M, total, W, hand, geo, un, vn, nm, bar_id, p);
+    if constexpr (M + 1 < F)
+        split_consumer_fill<T, K, K2, RX, M + 1, F>(total, W, hand, geo, un, vn, nm, bar_id, p);
 }
 
 // One work item per warp pair; `item` is the same for both warps of a pair.
@@ -130,6 +172,9 @@ __device__ __forceinline__ void temporal_split_item(int item, int bands, const T
     constexpr int K1 = K / 2;
     constexpr int K2 = K - K1;
     constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
+    // fill beats: the consumer's last stage starts computing at beat 2K + 1;
+    // whole 3-beat groups keep the window rotation's phase
+    constexpr int kFill = 3 * ((2 * K + 4) / 3);
     typedef typename Vec<T>::type VT;
     __shared__ __align__(16) VT ring_mem[kSplitPairs][kRing][2][32];
     __shared__ __align__(16) VT hand_mem[kSplitPairs][2][2][32];
@@ -156,10 +201,14 @@ __device__ __forceinline__ void temporal_split_item(int item, int bands, const T
             }
             cp_async_commit();
         }
-        for (int m = 0; m <= geo.total; m += 3) {
-            split_producer_beat<T, K1, RX, 0>(m, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v, bar_id, p);
-            split_producer_beat<T, K1, RX, 1>(m + 1, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v, bar_id, p);
-            split_producer_beat<T, K1, RX, 2>(m + 2, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v, bar_id, p);
+        split_producer_fill<T, K1, RX, 0, kFill>(geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v, bar_id, p);
+        for (int m = kFill; m <= geo.total; m += 3) {
+            split_producer_beat<T, K1, RX, kFill % 3>(m, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v,
+                                                      bar_id, p);
+            split_producer_beat<T, K1, RX, (kFill + 1) % 3>(m + 1, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc,
+                                                            u, v, bar_id, p);
+            split_producer_beat<T, K1, RX, (kFill + 2) % 3>(m + 2, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc,
+                                                            u, v, bar_id, p);
         }
         cp_async_wait<0>();
     } else {
@@ -168,10 +217,11 @@ __device__ __forceinline__ void temporal_split_item(int item, int bands, const T
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int s = 0; s < K2; ++s) zero_slice(W[a][s]);
-        for (int m = 0; m <= geo.total; m += 3) {
-            split_consumer_beat<T, K, K2, RX, 0>(m, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
-            split_consumer_beat<T, K, K2, RX, 1>(m + 1, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
-            split_consumer_beat<T, K, K2, RX, 2>(m + 2, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
+        split_consumer_fill<T, K, K2, RX, 0, kFill>(geo.total, W, hand, geo, un, vn, nm, bar_id, p);
+        for (int m = kFill; m <= geo.total; m += 3) {
+            split_consumer_beat<T, K, K2, RX, kFill % 3>(m, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
+            split_consumer_beat<T, K, K2, RX, (kFill + 1) % 3>(m + 1, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
+            split_consumer_beat<T, K, K2, RX, (kFill + 2) % 3>(m + 2, geo.total, W, hand, geo, un, vn, nm, bar_id, p);
         }
     }
 }
