@@ -99,8 +99,10 @@ enum { RDCNN_VARIANT_AUTO = 0,                    /* library's choice (temporal 
        RDCNN_VARIANT_TEMPORAL_WIDE = 5 };         /* temporal, 8 values per lane (k <= 4; not F64) */
 
 /* Launch shape: k = time steps fused per launch of the temporal kernels
- * (1..8 F32, 1..4 F64; 0 = library default), rows = grid rows each warp
- * walks (0 = library default).  Neither changes results, only speed. */
+ * (1..8 F32 / BF16 / F16, 1..4 F64, at most 4 for RDCNN_VARIANT_TEMPORAL_WIDE;
+ * 0 = library default), rows = grid rows each warp walks (0 = library
+ * default).  For F32 / F64 neither changes results, only speed; for 16-bit
+ * planes k is also the rounding interval (see above). */
 typedef struct rdcnn_tune {
     int k;
     int rows;
