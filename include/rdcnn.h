@@ -113,7 +113,8 @@ typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
 /* ------------------------------------------------------------------ single grid */
 
 /* Create a handle for an NN x NM grid (Sec. II.A: "NNxNM" array of cells).
- * nn, nm >= 1; p finite; boundary RDCNN_BC_PERIODIC/ZEROFLUX; dtype
+ * 1 <= nn, nm < 2^30 and nn * nm <= 2^40 (plane offsets are 64-bit; grids
+ * beyond 2^31 cells are supported); p finite; boundary RDCNN_BC_PERIODIC/ZEROFLUX; dtype
  * RDCNN_F32/F64; reaction RDCNN_REACTION_FHN/NONE/CENN.  Du, Dv >= 0 except
  * for CENN, whose feedback weights c and Du may have either sign (and which
  * gets no RDCNN_WARN_CFL check).  Pure host call (no CUDA work).

@@ -77,8 +77,10 @@ int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p, i
     if (!out) return set_error(RDCNN_EINVAL, "out is NULL");
     *out = nullptr;
     if (nn < 1 || nm < 1) return set_error(RDCNN_EINVAL, "grid size must be >= 1 (got %lld x %lld)", (long long)nn, (long long)nm);
-    if (nn > 0x7fffffff || nm > 0x7fffffff || nn * nm > (int64_t(1) << 40))
-        return set_error(RDCNN_EINVAL, "grid too large");
+    // each side below 2^30 (the kernels reflect indices modulo 2 NN and 2 NM in
+    // 32-bit arithmetic); plane offsets are 64-bit
+    if (nn >= (int64_t(1) << 30) || nm >= (int64_t(1) << 30) || nn * nm > (int64_t(1) << 40))
+        return set_error(RDCNN_EINVAL, "grid too large (each side < 2^30, at most 2^40 cells)");
     if (boundary != RDCNN_BC_PERIODIC && boundary != RDCNN_BC_ZEROFLUX)
         return set_error(RDCNN_EINVAL, "boundary must be RDCNN_BC_PERIODIC or RDCNN_BC_ZEROFLUX");
     if (dtype != RDCNN_F32 && dtype != RDCNN_F64 && dtype != RDCNN_BF16 && dtype != RDCNN_F16)

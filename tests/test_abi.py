@@ -73,6 +73,11 @@ def test_create_validation(lib, L):
     assert _create(lib, L, nn=0)[0] == L.EINVAL
     assert _create(lib, L, nm=-3)[0] == L.EINVAL
     assert _create(lib, L, boundary=2)[0] == L.EINVAL
+    assert _create(lib, L, nn=1 << 30, nm=4)[0] == L.EINVAL
+    assert _create(lib, L, nn=1 << 21, nm=1 << 20)[0] == L.EINVAL  # 2^41 cells
+    rc, h = _create(lib, L, nn=(1 << 30) - 1, nm=4)
+    assert rc == L.OK
+    lib.rdcnn_destroy(h)
     assert _create(lib, L, dtype=7)[0] == L.EINVAL
     assert _create(lib, L, reaction=5)[0] == L.EINVAL
     bad = {"dt": 0.1, "a": math.nan, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0}
