@@ -29,7 +29,10 @@
 namespace rdk {
 
 constexpr int kTemporalWarps = 4;  // warps per block of every kernel built on temporal_strip
-constexpr int kRing = 4;           // input rows staged per warp (prefetch distance kRing - 1)
+// Input rows staged per warp (prefetch distance kRing - 1 = 2 beats, about
+// 1.5 us of the K = 8 pipeline, above the HBM latency).  Three slots match
+// the 3-beat window rotation, so a beat's slots are compile-time constants.
+constexpr int kRing = 3;
 
 // Per-lane 16-byte asynchronous global -> shared copy (cp.async, L2 only).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -54,41 +57,53 @@ template <typename T> struct RowRing {
 };
 
 template <typename T>
-__device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, int nm, int lc,
-                                           const T *__restrict__ u, const T *__restrict__ v) {
+__device__ __forceinline__ void ring_issue_at(const RowRing<T> &r, int slot, int g, int nm, int lc,
+                                              const T *__restrict__ u, const T *__restrict__ v) {
     const int lane = threadIdx.x & 31;
     const int64_t off = (int64_t)g * nm + lc;
     if constexpr (sizeof(typename Vec<T>::type) == 32) {  // two 16-byte halves per field
-        char *su = reinterpret_cast<char *>(&r.slot[m % kRing][0][lane]);
-        char *sv = reinterpret_cast<char *>(&r.slot[m % kRing][1][lane]);
+        char *su = reinterpret_cast<char *>(&r.slot[slot][0][lane]);
+        char *sv = reinterpret_cast<char *>(&r.slot[slot][1][lane]);
         cp_async16(su, u + off);
         cp_async16(su + 16, reinterpret_cast<const char *>(u + off) + 16);
         cp_async16(sv, v + off);
         cp_async16(sv + 16, reinterpret_cast<const char *>(v + off) + 16);
     } else if constexpr (sizeof(typename Vec<T>::type) == 16) {
-        cp_async16(&r.slot[m % kRing][0][lane], u + off);
-        cp_async16(&r.slot[m % kRing][1][lane], v + off);
+        cp_async16(&r.slot[slot][0][lane], u + off);
+        cp_async16(&r.slot[slot][1][lane], v + off);
     } else {
-        cp_async8(&r.slot[m % kRing][0][lane], u + off);
-        cp_async8(&r.slot[m % kRing][1][lane], v + off);
+        cp_async8(&r.slot[slot][0][lane], u + off);
+        cp_async8(&r.slot[slot][1][lane], v + off);
     }
+}
+
+// Input row m goes to slot m % kRing.
+template <typename T>
+__device__ __forceinline__ void ring_issue(const RowRing<T> &r, int m, int g, int nm, int lc,
+                                           const T *__restrict__ u, const T *__restrict__ v) {
+    ring_issue_at(r, m % kRing, g, nm, lc, u, v);
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_read_at(const RowRing<T> &r, int slot, Slice<CT<T>, Vec<T>::N> &s) {
+    typedef typename Vec<T>::type VT;
+    const int lane = threadIdx.x & 31;
+    const VT a = r.slot[slot][0][lane];
+    const VT b = r.slot[slot][1][lane];
+    unpack_vec<T, Vec<T>::N>(a, s.u);
+    unpack_vec<T, Vec<T>::N>(b, s.v);
 }
 
 template <typename T>
 __device__ __forceinline__ void ring_read(const RowRing<T> &r, int m, Slice<CT<T>, Vec<T>::N> &s) {
-    typedef typename Vec<T>::type VT;
-    const int lane = threadIdx.x & 31;
-    const VT a = r.slot[m % kRing][0][lane];
-    const VT b = r.slot[m % kRing][1][lane];
-    unpack_vec<T, Vec<T>::N>(a, s.u);
-    unpack_vec<T, Vec<T>::N>(b, s.v);
+    ring_read_at(r, m % kRing, s);
 }
 
 // ring_read for boundary BC; under BC_MIRROR a lane whose columns lie beyond
 // an edge (rev) reverses the element order of the mirrored vector it loaded.
 template <typename T, int BC>
-__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int m, bool rev, Slice<CT<T>, Vec<T>::N> &s) {
-    ring_read(r, m, s);
+__device__ __forceinline__ void ring_read_bc(const RowRing<T> &r, int slot, bool rev, Slice<CT<T>, Vec<T>::N> &s) {
+    ring_read_at(r, slot, s);
     if constexpr (BC == BC_MIRROR) {
         constexpr int V = Vec<T>::N;
         Slice<CT<T>, Vec<T>::N> t = s;
@@ -157,15 +172,16 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec
     if (m >= total) return;
     // The slot written here was read in the previous beat, whose stage
     // computations (issued before this point) consumed that value.
+    static_assert(kRing == 3, "slots follow the 3-beat phase: row m sits in slot m % 3 == PH");
     if (m + kRing - 1 < total) {
-        ring_issue(ring, m + kRing - 1, walk.g, nm, lc, u, v);
+        ring_issue_at(ring, (PH + kRing - 1) % kRing, walk.g, nm, lc, u, v);
         walk.next(nn);
         pol.issue(m + kRing - 1);
     }
     cp_async_commit();
     cp_async_wait<kRing - 1>();  // the group holding row m is complete
     Slice<CT<T>, Vec<T>::N> cur;
-    ring_read_bc<T, BC>(ring, m, rev, cur);
+    ring_read_bc<T, BC>(ring, PH, rev, cur);
     pol.begin_beat(m);
 #pragma unroll
     for (int s = 0; s < K; ++s) {
