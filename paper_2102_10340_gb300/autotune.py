@@ -11,7 +11,7 @@ import torch
 
 _cache: dict = {}
 
-GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (0, 32, 64, 128, 256)] + \
+GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (0, 8, 16, 32, 64, 128, 256)] + \
                       [("temporal2", k, r) for k in (4, 6, 8) for r in (0, 64, 176, 256)] + \
                       [("temporal_wide", k, r) for k in (2, 3, 4) for r in (0, 32, 64, 128)] + \
                       [("step1", 1, r) for r in (4, 8, 16, 32)]
