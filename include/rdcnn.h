@@ -164,7 +164,11 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
  * in speed.  For BF16 / F16 every launch rounds the state once when it
  * stores it, so results depend on the steps per launch (k for TEMPORAL, 1
  * for STEP1 and GENERIC); variants with the same k agree bit for bit.
- * T = 0 is a no-op.  Asynchronous on the bound stream.  The vectorised
+ * T = 0 is a no-op.  Asynchronous on the bound stream.  Runs of small grids
+ * (cells x k <= 2^23) with at least 64 full-depth launches replay a CUDA
+ * graph of 32 captured launches (captured once per launch configuration on a
+ * stream the handle owns; not while the bound stream is being captured):
+ * the same kernels, the same bits, less launch overhead.  The vectorised
  * variants need NM to be a multiple of 4 (F32, BF16, F16) or 2 (F64) and
  * 16-byte (8-byte for BF16 / F16) aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns

@@ -19,6 +19,7 @@ std::atomic<uint64_t> g_launches{0};
 }  // namespace
 
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
@@ -221,6 +222,86 @@ static bool planes_ok(const rdcnn_t *h, int width, size_t align) {
 static bool vec_ok_for(const rdcnn_t *h) { return planes_ok(h, vec_width(h->dtype), vec_align(h->dtype)); }
 static bool wide_ok_for(const rdcnn_t *h) { return planes_ok(h, 8, 16); }
 
+// One launch of the resolved variant: kk steps from (cu, cv) into (nu, nv).
+static cudaError_t launch_one(const rdcnn_t *h, int variant, int kk, const void *cu, const void *cv, void *nu,
+                              void *nv, cudaStream_t s) {
+    if (variant == RDCNN_VARIANT_TEMPORAL_WIDE)
+        return launch_temporal_wide(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                                    h->tune_rows, s);  // 0 = chosen by the launcher
+    if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
+        return launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                                     h->tune_rows, s);
+    if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
+        return launch_temporal(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                               h->tune_rows, s);
+    if (variant == RDCNN_VARIANT_STEP1)
+        return launch_step1(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p,
+                            h->tune_rows ? h->tune_rows : default_rows_step1(h->dtype, h->nn, h->nm), s);
+    return launch_generic(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p, s);
+}
+
+// Graph replay for launch-bound runs: grids whose launches are short
+// (cells x k <= 2^23) spend a large share of each launch in launch overhead.
+// kGraphLaunches consecutive full-depth launches (an even count, so the state
+// is back in the bound planes after them) are captured once per launch
+// configuration on a private stream and replayed on the bound stream.  Same
+// kernels with the same arguments: the same bits as the plain launches.
+constexpr int kGraphLaunches = 32;
+
+static bool same_key(const rdcnn::GraphKey &a, const rdcnn::GraphKey &b) {
+    return a.u == b.u && a.v == b.v && a.su == b.su && a.sv == b.sv && a.variant == b.variant && a.k == b.k &&
+           a.rows == b.rows && a.dtype == b.dtype && a.reaction == b.reaction && a.boundary == b.boundary &&
+           std::memcmp(&a.p, &b.p, sizeof(rdcnn_params)) == 0;
+}
+
+static void drop_graph(rdcnn_t *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+// Capture (or reuse) the graph of kGraphLaunches launches of depth k for h's
+// current configuration.  Returns false when graphs cannot be used here; the
+// caller then launches normally.
+static bool ensure_graph(rdcnn_t *h, int variant, int k, void *su, void *sv) {
+    const rdcnn::GraphKey key{h->u, h->v, su, sv, variant, k, h->tune_rows, h->dtype, h->reaction, h->boundary, h->p};
+    if (h->graph && same_key(key, h->graph_key)) return true;
+    drop_graph(h);
+    if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->capture_stream = nullptr;
+        return false;
+    }
+    // launch-shape queries (occupancy) happen here, outside the capture
+    (void)plan_rows(h->dtype, h->reaction, h->boundary, variant, k, h->nn, h->nm, h->tune_rows);
+    if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    const void *cu = h->u, *cv = h->v;
+    void *nu = su, *nv = sv;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphLaunches && e == cudaSuccess; ++i) {
+        e = launch_one(h, variant, k, cu, cv, nu, nv, h->capture_stream);
+        const void *tu = cu, *tv = cv;
+        cu = nu; cv = nv;
+        nu = const_cast<void *>(tu); nv = const_cast<void *>(tv);
+    }
+    uncount_launches(kGraphLaunches);  // recorded, not run
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && ec == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || ec != cudaSuccess || !exec) {
+        (void)cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        return false;
+    }
+    h->graph = exec;
+    h->graph_key = key;
+    return true;
+}
+
 int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn mark, void *ctx) {
     if (!h) return set_error(RDCNN_EINVAL, "handle is NULL");
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
@@ -236,27 +317,26 @@ int run_core(rdcnn_t *h, int64_t T, int variant, int k, int64_t every, MarkFn ma
     const void *cu = h->u, *cv = h->v;
     void *nu = su, *nv = sv;
     int64_t left = T;
+    // launch-bound runs: replay whole groups of full-depth launches as a graph
+    const int64_t full = T / k;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (every == 0 && !mark && full >= 2 * kGraphLaunches && h->nn * h->nm * (int64_t)k <= (int64_t(1) << 23) &&
+        cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone &&
+        ensure_graph(h, variant, k, su, sv)) {
+        const int64_t reps = full / kGraphLaunches;
+        for (int64_t r = 0; r < reps; ++r) {
+            const cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+            if (e != cudaSuccess) return cuda_error(e, "graph launch");
+            count_launches(kGraphLaunches);
+        }
+        left -= reps * kGraphLaunches * (int64_t)k;  // the state is back in (u, v)
+    }
+    (void)cudaGetLastError();  // a refused capture query leaves nothing pending
     while (left > 0) {
         int kk = (int)(left < k ? left : k);
         const int64_t done = T - left;
         if (every > 0) kk = (int)std::min<int64_t>(kk, every - done % every);
-        cudaError_t e;
-        if (variant == RDCNN_VARIANT_TEMPORAL_WIDE)
-            e = launch_temporal_wide(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm,
-                                     h->p, h->tune_rows, h->stream);  // 0 = chosen by the launcher
-        else if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
-            e = launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
-                                      h->tune_rows, h->stream);  // 0 = chosen by the launcher
-        else if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
-            e = launch_temporal(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm,
-                                h->p, h->tune_rows, h->stream);  // 0 = chosen by the launcher
-        else if (variant == RDCNN_VARIANT_STEP1)
-            e = launch_step1(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p,
-                             h->tune_rows ? h->tune_rows : default_rows_step1(h->dtype, h->nn, h->nm),
-                             h->stream);
-        else
-            e = launch_generic(h->dtype, h->reaction, h->boundary, cu, cv, nu, nv, h->nn, h->nm, h->p,
-                               h->stream);
+        const cudaError_t e = launch_one(h, variant, kk, cu, cv, nu, nv, h->stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel launch");
         const void *tu = cu, *tv = cv;
         cu = nu; cv = nv;
@@ -308,6 +388,8 @@ int rdcnn_get_state(rdcnn_t *h, void *u_out, void *v_out, int to_device) {
 
 void rdcnn_destroy(rdcnn_t *h) {
     if (!h) return;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
 }

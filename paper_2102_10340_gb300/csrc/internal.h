@@ -20,6 +20,15 @@ struct rdcnn {
     bool bound = false;
     int tune_k = 0, tune_rows = 0;
     cudaStream_t copy_stream = nullptr;  // created on first use by rdcnn_run_snapshots
+    // Graph replay of runs of small grids (run_core): a captured sequence of
+    // full-depth launches and what it was captured for.
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    struct GraphKey {
+        const void *u, *v, *su, *sv;
+        int variant, k, rows, dtype, reaction, boundary;
+        rdcnn_params p;
+    } graph_key{};
 };
 
 namespace rdk {
@@ -51,6 +60,7 @@ inline int temporal_out_cols(int dtype, int k) {
 }
 
 void count_launches(uint64_t n);
+void uncount_launches(uint64_t n);  // launches recorded into a graph, not run
 
 // Error reporting (thread-local message, returned code passes through).
 int set_error(int code, const char *fmt, ...);
