@@ -42,8 +42,10 @@
  *    offset i * NM + j; i is the row (NN rows), j the column (NM columns).
  *  - Element type: float (RDCNN_F32) or double (RDCNN_F64), fixed per handle.
  *  - Memory ownership: the CALLER owns every buffer, host or device.  The
- *    library never allocates device memory; scratch space is passed in by
- *    the caller, sized by the matching *_workspace_bytes query.
+ *    library allocates no device buffers; scratch space is passed in by the
+ *    caller, sized by the matching *_workspace_bytes query.  A handle creates
+ *    only CUDA objects of its own (streams for snapshot copies and graph
+ *    capture, one graph executable), released by rdcnn_destroy.
  *  - Streams: work is enqueued on the caller's CUDA stream (cudaStream_t
  *    passed as void*; NULL = legacy default stream).  Calls that return data
  *    to host memory synchronise that stream before returning; all other calls
