@@ -238,3 +238,30 @@ def test_wide_variant_rejects_unsupported_planes(rd):
     with pytest.raises(rd.RDCNNError):
         g.run(4, variant="temporal_wide", k=2)
     g.close()
+
+
+@pytest.mark.parametrize("variant,k", [("generic", 0), ("step1", 0), ("temporal", 8)])
+def test_degenerate_genes(rd, oracle_mod, variant, k):
+    """dt = 0 leaves the state bitwise unchanged; Du = Dv = 0 decouples the cells, each then
+    following the oracle's scalar map (FP64, cell by cell)."""
+    x = inp.uniform_field(21, 24, 40)
+    y = inp.uniform_field(22, 24, 40)
+    still = dict(inp.default_params(), dt=0.0)
+    u, v = gpu_run(rd, x, y, still, 64, F64, variant, k)
+    assert np.array_equal(u, x) and np.array_equal(v, y)
+    apart = dict(inp.default_params(), Du=0.0, Dv=0.0)
+    u, v = gpu_run(rd, x, y, apart, 50, F64, variant, k)
+    for i, j in ((0, 0), (5, 17), (23, 39), (11, 3)):
+        su, sv = oracle_mod.scalar_map(x[i, j], y[i, j], apart, 50)
+        assert abs(u[i, j] - su[-1]) <= 1e-12 and abs(v[i, j] - sv[-1]) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(1, 64), (57, 4), (1, 4), (2, 8)])
+def test_single_row_and_column_tori(rd, oracle_mod, shape):
+    """One-row (or few-column) tori: a cell is its own north and south neighbour; the temporal
+    pipeline's halo rows all wrap to the same rows."""
+    x = inp.uniform_field(23, *shape)
+    ref = oracle_mod.run(x, -x, inp.default_params(), 33)
+    for variant, k in (("step1", 0), ("temporal", 3), ("temporal", 4)):
+        u, v = gpu_run(rd, x, -x, inp.default_params(), 33, F64, variant, k)
+        assert normwise(u, ref[0]) <= 1e-12 and normwise(v, ref[1]) <= 1e-12, (variant, k)
