@@ -311,10 +311,12 @@ struct ForwardPolicy {
     }
     __device__ __forceinline__ void finish(int q, const Slice<CT<T>, Vec<T>::N> &out) {
         const int orow = q - K;
-        if (orow >= 0 && geo.st_lane) {
+        if (orow >= 0) {  // the same for the whole warp
             const int64_t off = (int64_t)(geo.r0 + orow) * nm + geo.sc;
-            store_vec<T>(un + off, out.u);
-            store_vec<T>(vn + off, out.v);
+            if (geo.st_lane) {
+                store_vec<T>(un + off, out.u);
+                store_vec<T>(vn + off, out.v);
+            }
         }
     }
 };
