@@ -280,13 +280,14 @@ static bool ensure_graph(rdcnn_t *h, int variant, int k, void *su, void *sv) {
     const void *cu = h->u, *cv = h->v;
     void *nu = su, *nv = sv;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kGraphLaunches && e == cudaSuccess; ++i) {
+    int issued = 0;
+    for (int i = 0; i < kGraphLaunches && e == cudaSuccess; ++i, ++issued) {
         e = launch_one(h, variant, k, cu, cv, nu, nv, h->capture_stream);
         const void *tu = cu, *tv = cv;
         cu = nu; cv = nv;
         nu = const_cast<void *>(tu); nv = const_cast<void *>(tv);
     }
-    uncount_launches(kGraphLaunches);  // recorded, not run
+    uncount_launches((uint64_t)issued);  // recorded, not run (each launcher counted itself)
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &g);
     cudaGraphExec_t exec = nullptr;

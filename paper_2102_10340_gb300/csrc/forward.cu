@@ -1,6 +1,8 @@
-// forward.cu -- forward kernels for Eq. 1-3 (Sec. II.A) on a torus.
+// forward.cu -- forward kernels for Eq. 1-3 (Sec. II.A) and the launchers of
+// every forward variant (torus or zero flux; FitzHugh-Nagumo, pure diffusion
+// or CeNN cell; float / double planes, or bf16 / half planes computed in FP32).
 //
-//  k_step1     one time step per launch.  A warp owns a band of 32*V columns
+//  k_step1     one time step per launch (float / double planes).  A warp owns a band of 32*V columns
 //              (V = 4 floats / 2 doubles per lane, one 16-byte load) and walks
 //              down a strip of rows, keeping rows i-1, i, i+1 in registers and
 //              prefetching row i+2.  Horizontal neighbours come from the
@@ -19,7 +21,8 @@
 //  k_generic   one thread per cell, scalar loads: any size and alignment.
 //
 // All three evaluate cells with rdk::cell_update, so they produce identical
-// bits for identical inputs.  Under the zero-flux boundary the single-step
+// bits for identical inputs (for 16-bit planes: at the same steps per
+// launch, which is also the rounding interval).  Under the zero-flux boundary the single-step
 // and generic kernels clamp neighbour indices into the grid (the ghost cell
 // is the edge cell); the temporal kernel loads mirrored halos instead
 // (temporal.cuh).  k_temporal's launchers live in temporal_launch.cuh and are
