@@ -236,3 +236,38 @@ def test_create_accepts_16bit_storage(lib, L):
         assert lib.rdcnn_adjoint_workspace_bytes(h, 10, 0, ctypes.byref(nbytes)) == L.EINVAL
         lib.rdcnn_destroy(h)
     assert _create(lib, L, dtype=4)[0] == L.EINVAL
+
+
+def test_snapshot_summary_and_static_validation(lib, L):
+    """Host-side rejections of rdcnn_run_snapshots, rdcnn_batch_summary and rdcnn_run_static
+    (fake, never-dereferenced addresses; every case fails before any CUDA work)."""
+    p = L.params_struct({"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0})
+    assert lib.rdcnn_run_snapshots(None, 10, 2, 256, 512, 1, None, 0) == L.EINVAL
+    rc, h = _create(lib, L, nn=4, nm=8)
+    assert lib.rdcnn_run_snapshots(h, 10, 2, 256, 512, 1, None, 0) == L.ESTATE  # unbound
+    assert lib.rdcnn_bind(h, 256, 512, 1024, 1 << 12, None) == L.OK
+    assert lib.rdcnn_run_snapshots(h, 10, 0, 256, 512, 1, None, 0) == L.EINVAL  # every < 1
+    assert lib.rdcnn_run_snapshots(h, -1, 2, 256, 512, 1, None, 0) == L.EINVAL
+    assert lib.rdcnn_run_snapshots(h, 10, 2, None, 512, 1, None, 0) == L.EINVAL
+    assert lib.rdcnn_run_snapshots(h, 10, 2, 256, 512, 0, 4096, 16) == L.ESPACE  # staging too small
+    lib.rdcnn_destroy(h)
+
+    tab = (L.Instance * 1)()
+    tab[0] = L.Instance(8, 8, p, 256, 512, 0, 0)
+    out = (ctypes.c_double * 8)()
+    need = ctypes.c_size_t()
+    assert lib.rdcnn_summary_workspace_bytes(tab, 0, ctypes.byref(need)) == L.EINVAL
+    assert lib.rdcnn_summary_workspace_bytes(tab, 1, ctypes.byref(need)) == L.OK and need.value > 0
+    assert lib.rdcnn_batch_summary(tab, 1, L.BF16, 0.05, out, 4096, need.value, None) == L.EINVAL
+    assert lib.rdcnn_batch_summary(tab, 1, L.F32, 0.05, out, 4096, 8, None) == L.ESPACE
+    tab[0] = L.Instance(8, 8, p, 0, 512, 0, 0)
+    assert lib.rdcnn_batch_summary(tab, 1, L.F32, 0.05, out, 4096, need.value, None) == L.EINVAL
+
+    assert lib.rdcnn_run_static(0, 8, ctypes.byref(p), L.F32, L.REACTION_FHN, 256, 512, 10, 0, None) == L.EINVAL
+    assert lib.rdcnn_run_static(8, 8, ctypes.byref(p), L.BF16, L.REACTION_FHN, 256, 512, 10, 0, None) == L.EINVAL
+    assert lib.rdcnn_run_static(8, 8, ctypes.byref(p), L.F32, L.REACTION_CENN, 256, 512, 10, 0, None) == L.EINVAL
+    assert lib.rdcnn_run_static(8, 8, ctypes.byref(p), L.F32, L.REACTION_FHN, None, 512, 10, 0, None) == L.EINVAL
+    big = L.STATIC_SCRATCH_BYTES // 8 + 1  # one FP32 plane over half the static scratch
+    assert lib.rdcnn_run_static(1, big, ctypes.byref(p), L.F32, L.REACTION_FHN, 256, 512, 10, 0, None) == L.EINVAL
+    assert lib.rdcnn_run_static(8, 8, ctypes.byref(p), L.F32, L.REACTION_FHN, 256, 512, 10, 9, None) == L.EINVAL
+    assert lib.rdcnn_run_static(8, 8, ctypes.byref(p), L.F32, L.REACTION_FHN, 256, 512, 0, 0, None) == L.OK
