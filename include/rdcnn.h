@@ -252,6 +252,16 @@ int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int
                     const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
                     void *stream);
 
+/* rdcnn_batch_run with the model variants: boundary RDCNN_BC_PERIODIC or
+ * RDCNN_BC_ZEROFLUX, reaction FHN / NONE / CENN (the CeNN gene may carry
+ * feedback weights of either sign), shared by all instances.  FP32 supports
+ * every combination; FP64 the periodic FHN / NONE ones (RDCNN_EINVAL
+ * otherwise).  rdcnn_batch_run(...) == rdcnn_batch_run_model(...,
+ * RDCNN_BC_PERIODIC, ...). */
+int rdcnn_batch_run_model(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction,
+                          int boundary, const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
+                          void *stream);
+
 /* Statistics of every instance's state, computed on the device for ranking
  * the instances of a parameter search (Sec. III.A sorts (Du, Dv) into slow
  * growth, dynamic patterns and dull homogeneous states; Sec. III.B searches

@@ -77,6 +77,8 @@ SIGNATURES = [
                                             ctypes.POINTER(c_size)]),
     ("rdcnn_batch_run", c_int, [ctypes.POINTER(Instance), c_int, c_i64, c_int, c_int, ctypes.POINTER(Tune),
                                 c_vp, c_size, c_vp]),
+    ("rdcnn_batch_run_model", c_int, [ctypes.POINTER(Instance), c_int, c_i64, c_int, c_int, c_int,
+                                      ctypes.POINTER(Tune), c_vp, c_size, c_vp]),
     ("rdcnn_summary_workspace_bytes", c_int, [ctypes.POINTER(Instance), c_int, ctypes.POINTER(c_size)]),
     ("rdcnn_batch_summary", c_int, [ctypes.POINTER(Instance), c_int, c_int, c_double, ctypes.POINTER(c_double),
                                     c_vp, c_size, c_vp]),

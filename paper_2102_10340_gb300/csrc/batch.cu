@@ -1,5 +1,6 @@
 // batch.cu -- many independent RD-CNN instances (a parameter sweep in the
-// sense of Sec. III.A-III.B) advanced by ONE launch per K time steps.
+// sense of Sec. III.A-III.B) advanced by ONE launch per K time steps: the
+// host side (kernels in batch_kernels.cuh, instantiated in batch_*.cu).
 //
 // The host lays the instances out as a table of descriptors in device memory
 // with a running warp offset: instance i owns warps
@@ -19,83 +20,45 @@
 #include "common.cuh"
 #include "internal.h"
 #include "temporal.cuh"
+#include "batch_kernels.cuh"
+
+// the kernels compile in batch_f32a.cu .. batch_f32c.cu and batch_f64.cu
+RDK_EXTERN_BATCH(float, 1, 1) RDK_EXTERN_BATCH(float, 2, 1) RDK_EXTERN_BATCH(float, 3, 1)
+RDK_EXTERN_BATCH(float, 4, 1)
+RDK_EXTERN_BATCH(float, 1, 2) RDK_EXTERN_BATCH(float, 2, 2) RDK_EXTERN_BATCH(float, 3, 2)
+RDK_EXTERN_BATCH(float, 4, 2) RDK_EXTERN_BATCH(float, 5, 2) RDK_EXTERN_BATCH(float, 6, 2)
+RDK_EXTERN_BATCH(float, 7, 2) RDK_EXTERN_BATCH(float, 8, 2)
+RDK_EXTERN_BATCH(double, 1, 1) RDK_EXTERN_BATCH(double, 2, 1)
+RDK_EXTERN_BATCH(double, 1, 2) RDK_EXTERN_BATCH(double, 2, 2) RDK_EXTERN_BATCH(double, 3, 2)
+RDK_EXTERN_BATCH(double, 4, 2)
 
 namespace rdk {
 
 namespace {
 
-constexpr int kBatchBlock = 32 * kTemporalWarps;
-
-struct BatchDesc {
-    const void *u, *v;
-    void *su, *sv;
-    int nn, nm, bands, rows;
-    long long warp_begin;
-    double dt, Du, Dv, cm4, mthird, meps, ebm4, mepsa;  // as Coef<double>
-};
-
-template <typename T, int K, int H, int RX>
-__global__ void __launch_bounds__(kBatchBlock)
-k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int flip) {
-    const long long wid = (long long)blockIdx.x * (kBatchBlock / 32) + (threadIdx.x >> 5);
-    if (wid >= nwarps) return;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tab[mid].warp_begin <= wid) lo = mid; else hi = mid - 1;
-    }
-    const BatchDesc &d = tab[lo];
-    const int local = (int)(wid - d.warp_begin);
-    const int bands = d.bands;
-    Coef<T> p;
-    p.dt = T(d.dt); p.Du = T(d.Du); p.Dv = T(d.Dv); p.cm4 = T(d.cm4);
-    p.mthird = T(d.mthird); p.meps = T(d.meps); p.ebm4 = T(d.ebm4); p.mepsa = T(d.mepsa);
-    const T *su = (const T *)(flip ? d.su : d.u);
-    const T *sv = (const T *)(flip ? d.sv : d.v);
-    T *du = (T *)(flip ? d.u : d.su);
-    T *dv = (T *)(flip ? d.v : d.sv);
-    temporal_strip<T, K, H, RX>(local % bands, local / bands, su, sv, du, dv, d.nn, d.nm, d.rows, p);
-}
-
-template <typename T, int K, int H>
-cudaError_t batch_launch_khr(int reaction, const BatchDesc *tab, int n, long long nwarps, int flip,
-                             cudaStream_t s) {
-    const int wpb = kBatchBlock / 32;
-    const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_batch_temporal<T, K, H, RX_FHN><<<grid, kBatchBlock, 0, s>>>(tab, n, nwarps, flip);
-    else
-        k_batch_temporal<T, K, H, RX_NONE><<<grid, kBatchBlock, 0, s>>>(tab, n, nwarps, flip);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
+// Depths 1 .. H*V for halo H.
 template <typename T, int H>
-cudaError_t batch_launch_h(int reaction, int k, const BatchDesc *tab, int n, long long nwarps,
+cudaError_t batch_launch_h(int reaction, int boundary, int k, const BatchDesc *tab, int n, long long nwarps,
                            int flip, cudaStream_t s) {
     constexpr int V = Vec<T>::N;
     if (k < 1 || k > H * V) return cudaErrorInvalidValue;
-    switch (k) {
-        case 1: return batch_launch_khr<T, 1, H>(reaction, tab, n, nwarps, flip, s);
-        case 2: return batch_launch_khr<T, 2, H>(reaction, tab, n, nwarps, flip, s);
-        case 3: if constexpr (H * V >= 3) return batch_launch_khr<T, 3, H>(reaction, tab, n, nwarps, flip, s); break;
-        case 4: if constexpr (H * V >= 4) return batch_launch_khr<T, 4, H>(reaction, tab, n, nwarps, flip, s); break;
-        case 5: if constexpr (H * V >= 5) return batch_launch_khr<T, 5, H>(reaction, tab, n, nwarps, flip, s); break;
-        case 6: if constexpr (H * V >= 6) return batch_launch_khr<T, 6, H>(reaction, tab, n, nwarps, flip, s); break;
-        case 7: if constexpr (H * V >= 7) return batch_launch_khr<T, 7, H>(reaction, tab, n, nwarps, flip, s); break;
-        case 8: if constexpr (H * V >= 8) return batch_launch_khr<T, 8, H>(reaction, tab, n, nwarps, flip, s); break;
-    }
-    return cudaErrorInvalidValue;
+    return with_depth(k, [&](auto kk) -> cudaError_t {
+        constexpr int K = decltype(kk)::value;
+        if constexpr (K <= H * V)
+            return batch_launch_khr<T, K, H>(reaction, boundary, tab, n, nwarps, flip, s);
+        else
+            return cudaErrorInvalidValue;
+    });
 }
 
-cudaError_t batch_launch(int dtype, int reaction, int k, int H, const BatchDesc *tab, int n,
+cudaError_t batch_launch(int dtype, int reaction, int boundary, int k, int H, const BatchDesc *tab, int n,
                          long long nwarps, int flip, cudaStream_t s) {
     if (dtype == RDCNN_F64) {
-        if (H == 1) return batch_launch_h<double, 1>(reaction, k, tab, n, nwarps, flip, s);
-        return batch_launch_h<double, 2>(reaction, k, tab, n, nwarps, flip, s);
+        if (H == 1) return batch_launch_h<double, 1>(reaction, boundary, k, tab, n, nwarps, flip, s);
+        return batch_launch_h<double, 2>(reaction, boundary, k, tab, n, nwarps, flip, s);
     }
-    if (H == 1) return batch_launch_h<float, 1>(reaction, k, tab, n, nwarps, flip, s);
-    return batch_launch_h<float, 2>(reaction, k, tab, n, nwarps, flip, s);
+    if (H == 1) return batch_launch_h<float, 1>(reaction, boundary, k, tab, n, nwarps, flip, s);
+    return batch_launch_h<float, 2>(reaction, boundary, k, tab, n, nwarps, flip, s);
 }
 
 int batch_default_rows(int64_t nn) { return nn >= 1024 ? 64 : 32; }
@@ -117,11 +80,15 @@ std::vector<int> plan_depths(int64_t T, int k) {
     return d;
 }
 
-int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, int *warn) {
+int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, int boundary, int *warn) {
     if (!inst || n < 1) return set_error(RDCNN_EINVAL, "need at least one instance");
     if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "bad dtype");
-    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE)
+    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE && reaction != RDCNN_REACTION_CENN)
         return set_error(RDCNN_EINVAL, "bad reaction");
+    if (boundary != RDCNN_BC_PERIODIC && boundary != RDCNN_BC_ZEROFLUX)
+        return set_error(RDCNN_EINVAL, "bad boundary");
+    if (dtype == RDCNN_F64 && (reaction == RDCNN_REACTION_CENN || boundary != RDCNN_BC_PERIODIC))
+        return set_error(RDCNN_EINVAL, "the FP64 batch supports the periodic FHN / NONE models only");
     const int V = vec_width(dtype);
     *warn = RDCNN_OK;
     for (int i = 0; i < n; ++i) {
@@ -134,7 +101,7 @@ int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, i
             return set_error(RDCNN_EINVAL, "instance %d: NULL plane", i);
         if (!aligned16(x.u) || !aligned16(x.v) || !aligned16(x.su) || !aligned16(x.sv))
             return set_error(RDCNN_EINVAL, "instance %d: planes must be 16-byte aligned", i);
-        const int pc = check_params(&x.params);
+        const int pc = check_params(&x.params, reaction);
         if (pc < 0) {
             char why[256];
             snprintf(why, sizeof(why), "%s", rdcnn_last_error());
@@ -174,8 +141,14 @@ int rdcnn_batch_workspace_bytes(const rdcnn_instance *inst, int n, int dtype,
 int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction,
                     const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
                     void *stream) {
+    return rdcnn_batch_run_model(inst, n, T, dtype, reaction, RDCNN_BC_PERIODIC, tune, workspace,
+                                 workspace_bytes, stream);
+}
+
+int rdcnn_batch_run_model(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction, int boundary,
+                          const rdcnn_tune *tune, void *workspace, size_t workspace_bytes, void *stream) {
     int warn = RDCNN_OK;
-    int rc = validate_batch(inst, n, dtype, reaction, &warn);
+    int rc = validate_batch(inst, n, dtype, reaction, boundary, &warn);
     if (rc < 0) return rc;
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     int k = 0, rows_req = 0;
@@ -213,7 +186,7 @@ int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int
     const std::vector<int> depths = plan_depths(T, k);
     int flip = 0;
     for (int kk : depths) {
-        e = batch_launch(dtype, reaction, kk, H, (const BatchDesc *)workspace, n, warps, flip, s);
+        e = batch_launch(dtype, reaction, boundary, kk, H, (const BatchDesc *)workspace, n, warps, flip, s);
         if (e != cudaSuccess) return cuda_error(e, "batch kernel launch");
         flip ^= 1;
     }

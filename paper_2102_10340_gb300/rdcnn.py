@@ -315,11 +315,13 @@ class Batch:
     Each instance gets torch-owned device planes u, v and scratch su, sv.
     """
 
-    def __init__(self, instances, dtype=torch.float32, reaction: str = "fhn", device="cuda"):
+    def __init__(self, instances, dtype=torch.float32, reaction: str = "fhn", device="cuda",
+                 boundary: str = "periodic"):
         self.lib = L.load()
         self.dtype = dtype
         self.device = torch.device(device)
         self.reaction = reaction
+        self.boundary = boundary
         self.items = []
         for spec in instances:
             nn, nm = int(spec["nn"]), int(spec["nm"])
@@ -355,10 +357,11 @@ class Batch:
 
     def run(self, T: int):
         """Advance every instance by T steps of Eq. 1 (asynchronous after the table upload)."""
-        rc = L.check(self.lib.rdcnn_batch_run(self._table, len(self.items), int(T), _dtype_code(self.dtype),
-                                              _REACTIONS[self.reaction], ctypes.byref(self.tune),
-                                              _vp(self.workspace), self.workspace.numel(),
-                                              ctypes.c_void_p(_stream_ptr(self.device))))
+        rc = L.check(self.lib.rdcnn_batch_run_model(self._table, len(self.items), int(T),
+                                                    _dtype_code(self.dtype), _REACTIONS[self.reaction],
+                                                    _BOUNDARIES[self.boundary], ctypes.byref(self.tune),
+                                                    _vp(self.workspace), self.workspace.numel(),
+                                                    ctypes.c_void_p(_stream_ptr(self.device))))
         _warn(rc)
         return self
 

@@ -46,8 +46,11 @@ def classify(traj: np.ndarray, flat: float = 1e-6, full: float = 0.5, growth: fl
 
 
 def sweep(genes, N: int = 256, T: int = 2000, init: str = "patch", checkpoints: int = 4, seed: int = 0,
-          dtype=torch.float32, threshold: float = 0.05, tune: dict | None = None, device="cuda"):
-    """Run every gene in ``genes`` (list of dicts) on an N x N torus for T steps.
+          dtype=torch.float32, threshold: float = 0.05, tune: dict | None = None, device="cuda",
+          reaction: str = "fhn", boundary: str = "periodic"):
+    """Run every gene in ``genes`` (list of dicts) on an N x N grid for T steps (torus, or zero
+    flux with ``boundary="zeroflux"``; ``reaction="cenn"`` sweeps Chua-Yang cells, whose
+    offset plane v starts equal to the input like u).
 
     init: "patch" (16 x 16 U[-1, 1] square in the middle, the paper's typ=1 shape) or
     "random" (all cells U[-1, 1], typ=2), drawn from ``seed`` (same start for every gene).
@@ -62,7 +65,8 @@ def sweep(genes, N: int = 256, T: int = 2000, init: str = "patch", checkpoints: 
     else:
         raise ValueError("init must be 'patch' or 'random'")
     xt = torch.from_numpy(np.asarray(x)).to(dtype)
-    batch = rd.Batch([{"nn": N, "nm": N, "params": g} for g in genes], dtype=dtype, device=device)
+    batch = rd.Batch([{"nn": N, "nm": N, "params": g} for g in genes], dtype=dtype, device=device,
+                     reaction=reaction, boundary=boundary)
     for i in range(len(genes)):
         batch.set_state(i, xt, xt)
     if tune:

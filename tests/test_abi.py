@@ -132,6 +132,19 @@ def test_bound_run_rejects_bad_args_before_gpu_work(lib, L):
     lib.rdcnn_destroy(h)
 
 
+def test_batch_model_validation(lib, L):
+    p = L.params_struct({"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 2.0, "Du": -0.5, "Dv": 0.0})
+    tab = (L.Instance * 1)()
+    tab[0] = L.Instance(8, 8, p, 256, 512, 768, 1024)
+    run = lambda dt, rx, bc, ws=1 << 12: lib.rdcnn_batch_run_model(tab, 1, 0, dt, rx, bc, None, 4096, ws, None)
+    assert run(L.F32, L.REACTION_CENN, L.BC_ZEROFLUX) == L.OK  # T = 0: validation only
+    assert run(L.F32, L.REACTION_CENN, L.BC_PERIODIC) == L.OK
+    assert run(L.F32, L.REACTION_FHN, L.BC_ZEROFLUX) == L.EINVAL  # Du < 0 is a diffusion error here
+    assert run(L.F64, L.REACTION_CENN, L.BC_PERIODIC) == L.EINVAL
+    assert run(L.F32, L.REACTION_CENN, 2) == L.EINVAL
+    assert run(L.F32, 3, L.BC_PERIODIC) == L.EINVAL
+
+
 def test_batch_validation(lib, L):
     p = L.params_struct({"dt": 0.1, "a": -0.3, "b": 1.3, "eps": -0.1, "c": 1.0, "Du": 0.06, "Dv": 1.0})
     tab = (L.Instance * 2)()

@@ -83,3 +83,62 @@ def test_batch_rejects_bad_instance(rd):
     with pytest.raises(rd.RDCNNError):
         b = rd.Batch([{"nn": 8, "nm": 6}], dtype=F32)
         b.run(3)
+
+
+# Chua-Yang gene with moderate linear growth (as in test_gpu_models).
+CENN_GENE = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.2, "Du": 0.1, "Dv": 0.0}
+MODELS = [("fhn", "zeroflux"), ("none", "zeroflux"), ("cenn", "periodic"), ("cenn", "zeroflux")]
+
+
+@pytest.mark.parametrize("k", [1, 3, 4, 8])
+@pytest.mark.parametrize("model", MODELS, ids=[f"{r}-{b}" for r, b in MODELS])
+def test_batch_models_vs_oracle_and_single_grid(rd, oracle_mod, model, k):
+    """Zero-flux boundary and the CeNN cell in the batched sweep: the oracle within 1e-5
+    and the same bits as a single-grid run of each instance (T = 23, ragged last launch)."""
+    reaction, boundary = model
+    shapes = [(37, 64), (5, 8), (128, 132), (1, 4), (66, 260)]
+    specs = []
+    for i, (nn, nm) in enumerate(shapes):
+        gene = dict(CENN_GENE, Du=0.05 + 0.02 * i) if reaction == "cenn" else inp.default_params(Du=0.1 + 0.05 * i)
+        specs.append({"nn": nn, "nm": nm, "params": gene})
+    b = rd.Batch(specs, dtype=F32, reaction=reaction, boundary=boundary)
+    b.set_tune(k=k)
+    starts = []
+    for i, s in enumerate(specs):
+        x = inp.uniform_field(90 + i, s["nn"], s["nm"])
+        y = inp.uniform_field(190 + i, s["nn"], s["nm"])
+        u0, v0 = (f32(1.5 * x), f32(0.3 * y)) if reaction == "cenn" else (f32(x), f32(y))
+        b.set_state(i, torch.from_numpy(u0), torch.from_numpy(v0))
+        starts.append((u0, v0))
+    T = 23
+    b.run(T)
+    torch.cuda.synchronize()
+    rx = {"fhn": oracle_mod.FHN, "none": oracle_mod.NONE, "cenn": oracle_mod.CENN}[reaction]
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    for i, s in enumerate(specs):
+        u0, v0 = starts[i]
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        ref_u, ref_v = oracle_mod.run(u0, v0, s["params"], T, reaction=rx, boundary=bc)
+        assert normwise(u, ref_u) <= 1e-5 and normwise(v, ref_v) <= 1e-5, (i, s["nn"], s["nm"])
+        one = gpu_run(rd, u0, v0, s["params"], T, F32, "generic", reaction=reaction, boundary=boundary)
+        assert np.array_equal(u, one[0]) and np.array_equal(v, one[1]), (i, s["nn"], s["nm"])
+        if reaction == "cenn":
+            assert np.array_equal(v, v0)
+
+
+@pytest.mark.parametrize("model", [("fhn", "zeroflux"), ("cenn", "periodic")])
+def test_batch_f64_models_rejected(rd, model):
+    """The FP64 batched sweep is built for the torus FitzHugh-Nagumo and reaction-free models only."""
+    reaction, boundary = model
+    gene = CENN_GENE if reaction == "cenn" else inp.default_params()
+    b = rd.Batch([{"nn": 8, "nm": 8, "params": gene}], dtype=F64, reaction=reaction, boundary=boundary)
+    with pytest.raises(rd.RDCNNError):
+        b.run(3)
+
+
+def test_sweep_zero_flux_cenn(rd):
+    """search.sweep forwards the model variant to the batch."""
+    from paper_2102_10340_gb300 import search
+    genes = [dict(CENN_GENE, Du=d) for d in (0.05, 0.1)]
+    out = search.sweep(genes, N=64, T=40, reaction="cenn", boundary="zeroflux", checkpoints=2)
+    assert out["stats"].shape == (2, 3, 8) and np.isfinite(out["stats"]).all()
