@@ -170,7 +170,11 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
  * (cells x k <= 2^23) with at least 64 full-depth launches replay a CUDA
  * graph of 32 captured launches (captured once per launch configuration on a
  * stream the handle owns; not while the bound stream is being captured):
- * the same kernels, the same bits, less launch overhead.  The vectorised
+ * the same kernels, the same bits, less launch overhead.  The stepping
+ * kernels of every entry point are launched with programmatic dependent
+ * launch (each may be scheduled while the previous one drains, and reads
+ * nothing before it has completed); the environment variable RDCNN_PDL=0,
+ * read once per process, launches them plainly.  The vectorised
  * variants need NM to be a multiple of 4 (F32, BF16, F16) or 2 (F64) and
  * 16-byte (8-byte for BF16 / F16) aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns

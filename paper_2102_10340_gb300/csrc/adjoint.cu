@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kPipeBlock)
 k_adjoint_pipe(const T *__restrict__ lu, const T *__restrict__ lv, T *__restrict__ lun,
                T *__restrict__ lvn, StagePlanes<T> state, double *__restrict__ partial, int nn,
                int nm, int bands, int nwarps, int rows, AdjCoef<T> p) {
+    pdl_wait();
     const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
     if (wid >= nwarps) return;
     const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
@@ -192,6 +193,7 @@ k_adjoint_pipe(const T *__restrict__ lu, const T *__restrict__ lv, T *__restrict
     pol.init();
     pipeline_strip<T, K>(geo, lu, lv, nn, nm, pol);
     pol.flush(partial + (int64_t)wid * 6);
+    pdl_trigger();
 }
 
 // K forward steps from (u, v), storing the state after every step s+1 into
@@ -200,11 +202,13 @@ template <typename T, int K, int H, int RX>
 __global__ void __launch_bounds__(kPipeBlock)
 k_forward_all(const T *__restrict__ u, const T *__restrict__ v, StagePlanes<T> planes, int nn,
               int nm, int bands, int nwarps, int rows, Coef<T> p) {
+    pdl_wait();
     const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
     if (wid >= nwarps) return;
     const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
     ForwardAllPolicy<T, K, RX> pol{p, geo, planes, nm};
     pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
+    pdl_trigger();
 }
 
 // Sum per-warp partials (fixed order), scale by dt: out[q] = dt * sum_w partial[w][q].
@@ -274,16 +278,12 @@ cudaError_t reverse_launch_k(int reaction, const void *lu, const void *lv, void 
     const cudaError_t oe = reaction == RDCNN_REACTION_FHN ? pipe_smem_optin<T, K, RX_FHN>()
                                                           : pipe_smem_optin<T, K, RX_NONE>();
     if (oe != cudaSuccess) return oe;
-    if (reaction == RDCNN_REACTION_FHN)
-        k_adjoint_pipe<T, K, 1, RX_FHN><<<grid, kPipeBlock, smem, s>>>(
-            (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, st, partial, (int)nn, (int)nm,
-            sh.bands, sh.nwarps, sh.rows, c);
-    else
-        k_adjoint_pipe<T, K, 1, RX_NONE><<<grid, kPipeBlock, smem, s>>>(
-            (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn, st, partial, (int)nn, (int)nm,
-            sh.bands, sh.nwarps, sh.rows, c);
+    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_adjoint_pipe<T, K, 1, RX_FHN>
+                                                                 : k_adjoint_pipe<T, K, 1, RX_NONE>,
+                                   grid, kPipeBlock, smem, s, (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn,
+                                   st, partial, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T, int K>
@@ -292,14 +292,12 @@ cudaError_t forward_all_launch_k(int reaction, const void *u, const void *v, con
                                  cudaStream_t s) {
     const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const Coef<T> c = make_coef<T>(p, reaction);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_forward_all<T, K, 1, RX_FHN><<<grid, kPipeBlock, 0, s>>>(
-            (const T *)u, (const T *)v, pl, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
-    else
-        k_forward_all<T, K, 1, RX_NONE><<<grid, kPipeBlock, 0, s>>>(
-            (const T *)u, (const T *)v, pl, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
+    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_forward_all<T, K, 1, RX_FHN>
+                                                                 : k_forward_all<T, K, 1, RX_NONE>,
+                                   grid, kPipeBlock, 0, s, (const T *)u, (const T *)v, pl, (int)nn, (int)nm,
+                                   sh.bands, sh.nwarps, sh.rows, c);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 // Depth dispatch (depth <= V keeps one halo lane): F32 1..4, F64 1..2.

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -50,6 +51,14 @@ int check_params(const rdcnn_params *p, int reaction) {
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("RDCNN_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,
                 int *reaction, cudaStream_t *stream, int *boundary) {

@@ -28,6 +28,7 @@ struct BatchDesc {
 template <typename T, int K, int H, int RX, int BC>
 __global__ void __launch_bounds__(kBatchBlock)
 k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int flip) {
+    pdl_wait();
     const long long wid = (long long)blockIdx.x * (kBatchBlock / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;
     int lo = 0, hi = n - 1;
@@ -46,6 +47,7 @@ k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int
     T *du = (T *)(flip ? d.u : d.su);
     T *dv = (T *)(flip ? d.v : d.sv);
     temporal_strip<T, K, H, RX, BC>(local % bands, local / bands, su, sv, du, dv, d.nn, d.nm, d.rows, p);
+    pdl_trigger();
 }
 
 // One depth.  FP32: every model of the single-grid kernels; FP64: the
@@ -57,20 +59,18 @@ cudaError_t batch_launch_khr(int reaction, int boundary, const BatchDesc *tab, i
     const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
     if constexpr (std::is_same<T, double>::value) {
         if (boundary != RDCNN_BC_PERIODIC) return cudaErrorInvalidValue;
-        if (reaction == RDCNN_REACTION_FHN)
-            k_batch_temporal<T, K, H, RX_FHN, BC_WRAP><<<grid, kBatchBlock, 0, s>>>(tab, n, nwarps, flip);
-        else if (reaction == RDCNN_REACTION_NONE)
-            k_batch_temporal<T, K, H, RX_NONE, BC_WRAP><<<grid, kBatchBlock, 0, s>>>(tab, n, nwarps, flip);
-        else
-            return cudaErrorInvalidValue;
+        if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_batch_temporal<T, K, H, RX_FHN, BC_WRAP>
+                                                                      : k_batch_temporal<T, K, H, RX_NONE, BC_WRAP>,
+                                       grid, kBatchBlock, 0, s, tab, n, nwarps, flip);
         count_launches(1);
-        return cudaGetLastError();
+        return e;
     } else {
         return with_model(reaction, boundary, [&](auto rx, auto bc) {
-            k_batch_temporal<T, K, H, decltype(rx)::value, decltype(bc)::value><<<grid, kBatchBlock, 0, s>>>(
-                tab, n, nwarps, flip);
+            const cudaError_t e = launch_k(k_batch_temporal<T, K, H, decltype(rx)::value, decltype(bc)::value>,
+                                           grid, kBatchBlock, 0, s, tab, n, nwarps, flip);
             count_launches(1);
-            return cudaGetLastError();
+            return e;
         });
     }
 }

@@ -31,6 +31,19 @@ enum { BC_WRAP = 0, BC_MIRROR = 1 };
 
 template <int N> using IntC = std::integral_constant<int, N>;
 
+// Programmatic dependent launch.  A stepping kernel launched with the
+// programmatic-serialization attribute (launch_k in internal.h) may be
+// scheduled while the previous kernel of the stream is still draining.
+// pdl_wait() returns when the previous kernel has completed and its writes
+// are visible: every kernel launched this way calls it before its first
+// global memory access (reads and writes: the ping-pong planes are read by
+// one launch and overwritten by the next).  pdl_trigger(), called when a
+// thread's work is done, lets the next kernel be scheduled once every block
+// of this one has called it or exited, so its launch overlaps this kernel's
+// tail.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Host-side dispatch of a runtime (reaction, boundary) pair to a callable
 // taking the two as compile-time tags: f(IntC<RX>{}, IntC<BC>{}).
 template <class F>

@@ -50,6 +50,7 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
         T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<T> p) {
     constexpr int V = Vec<T>::N;
     constexpr bool zf = (BC == BC_MIRROR);
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * (kStep1Block / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;  // whole warps only
@@ -115,6 +116,7 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
         sw_u = pw_u; se_u = pe_u; sw_v = pw_v; se_v = pe_v;
         rs = rp;
     }
+    pdl_trigger();
 }
 
 // --------------------------------------------------------------------------- temporal blocking
@@ -125,9 +127,11 @@ template <typename T, int K, int RX>
 __global__ void __launch_bounds__(kSplitBlock)
 k_temporal_split(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
                  T *__restrict__ vn, int nn, int nm, int bands, int nitems, int rows, Coef<T> p) {
+    pdl_wait();
     const int item = blockIdx.x * kSplitPairs + ((threadIdx.x >> 5) >> 1);
     if (item >= nitems) return;  // the whole pair, before any barrier
     temporal_split_item<T, K, RX>(item, bands, u, v, un, vn, nn, nm, rows, p);
+    pdl_trigger();
 }
 
 // --------------------------------------------------------------------------- generic
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(256)
 k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
           T *__restrict__ vn, int nn, int nm, Coef<CT<T>> p) {
     constexpr bool zf = (BC == BC_MIRROR);
+    pdl_wait();
     const int64_t n = (int64_t)nn * nm;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -156,6 +161,7 @@ k_generic(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
         un[idx] = to_storage<T>(ou);
         vn[idx] = to_storage<T>(ov);
     }
+    pdl_trigger();
 }
 
 template <typename T>
@@ -190,10 +196,11 @@ cudaError_t step1_t(int reaction, int boundary, const void *u, const void *v, vo
         const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
         const Coef<T> c = make_coef<T>(p, reaction);
         return with_model(reaction, boundary, [&](auto rx, auto bc) {
-            k_step1<T, decltype(rx)::value, decltype(bc)::value><<<grid, kStep1Block, 0, s>>>(
-                (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, rows, c);
+            const cudaError_t e = launch_k(k_step1<T, decltype(rx)::value, decltype(bc)::value>, grid,
+                                           kStep1Block, 0, s, (const T *)u, (const T *)v, (T *)un, (T *)vn,
+                                           (int)nn, (int)nm, bands, (int)nwarps, rows, c);
             count_launches(1);
-            return cudaGetLastError();
+            return e;
         });
     }
 }
@@ -265,14 +272,12 @@ cudaError_t split_tk(int reaction, const void *u, const void *v, void *un, void 
     const int64_t nitems = (int64_t)bands * strips;
     const unsigned grid = (unsigned)((nitems + kSplitPairs - 1) / kSplitPairs);
     const Coef<T> c = make_coef<T>(p, reaction);
-    if (reaction == RDCNN_REACTION_FHN)
-        k_temporal_split<T, K, RX_FHN><<<grid, kSplitBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nitems, rows, c);
-    else
-        k_temporal_split<T, K, RX_NONE><<<grid, kSplitBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nitems, rows, c);
+    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_temporal_split<T, K, RX_FHN>
+                                                                 : k_temporal_split<T, K, RX_NONE>,
+                                   grid, kSplitBlock, 0, s, (const T *)u, (const T *)v, (T *)un, (T *)vn,
+                                   (int)nn, (int)nm, bands, (int)nitems, rows, c);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>
@@ -283,10 +288,10 @@ cudaError_t generic_t(int reaction, int boundary, const void *u, const void *v, 
     const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)sm_count() * 16);
     const Coef<CT<T>> c = make_coef<CT<T>>(p, reaction);
     return with_model(reaction, boundary, [&](auto rx, auto bc) {
-        k_generic<T, decltype(rx)::value, decltype(bc)::value><<<grid, 256, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, c);
+        const cudaError_t e = launch_k(k_generic<T, decltype(rx)::value, decltype(bc)::value>, grid, 256, 0, s,
+                                       (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, c);
         count_launches(1);
-        return cudaGetLastError();
+        return e;
     });
 }
 

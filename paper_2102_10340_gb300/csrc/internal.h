@@ -73,6 +73,31 @@ bool aligned16(const void *p);
 inline bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 int sm_count();
 
+// Programmatic dependent launch of the stepping kernels: on unless the
+// environment sets RDCNN_PDL=0 (read once).
+bool pdl_enabled();
+
+// Launch kernel<<<grid, block, smem, s>>>(args...), with the
+// programmatic-serialization attribute when pdl_enabled(): the kernel must
+// call pdl_wait() (common.cuh) before its first global memory access.
+// Returns the launch status.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // Read-only view of a handle's configuration (defined in api.cu); the stream
 // is the one bound by rdcnn_bind (NULL if unbound).
 int handle_view(const rdcnn_t *h, int64_t *nn, int64_t *nm, rdcnn_params *p, int *dtype,

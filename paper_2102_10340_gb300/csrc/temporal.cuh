@@ -373,10 +373,12 @@ template <typename T, int K, int RX, int BC>
 __global__ void __launch_bounds__(kTemporalBlock)
 k_temporal(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
            T *__restrict__ vn, int nn, int nm, int bands, int nwarps, int rows, Coef<CT<T>> p) {
+    pdl_wait();
     const int wid = blockIdx.x * (kTemporalBlock / 32) + (threadIdx.x >> 5);
     if (wid >= nwarps) return;  // whole warps only
     constexpr int H = (K + Vec<T>::N - 1) / Vec<T>::N;
     temporal_strip<T, K, H, RX, BC>(wid % bands, wid / bands, u, v, un, vn, nn, nm, rows, p);
+    pdl_trigger();
 }
 
 }  // namespace rdk

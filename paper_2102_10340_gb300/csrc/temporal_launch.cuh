@@ -57,10 +57,10 @@ cudaError_t temporal_launch(int reaction, int boundary, const void *u, const voi
         const int64_t nwarps = (int64_t)bands * strips;
         const int wpb = kTemporalBlock / 32;
         const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-        k_temporal<T, K, RX, BC><<<grid, kTemporalBlock, 0, s>>>(
-            (const T *)u, (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, r, c);
+        const cudaError_t e = launch_k(k_temporal<T, K, RX, BC>, grid, kTemporalBlock, 0, s, (const T *)u,
+                                       (const T *)v, (T *)un, (T *)vn, (int)nn, (int)nm, bands, (int)nwarps, r, c);
         count_launches(1);
-        return cudaGetLastError();
+        return e;
     });
 }
 
