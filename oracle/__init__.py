@@ -127,6 +127,9 @@ class Oracle:
         lib.oracle_adjoint.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, i64, dp, dp, i64,
                                        dp, dp, dp, ctypes.c_int]
         lib.oracle_adjoint.restype = ctypes.c_int
+        lib.oracle_adjoint_bc.argtypes = [i64, i64, dp, dp, dp, ctypes.c_int, ctypes.c_int, i64, dp, dp,
+                                          i64, dp, dp, dp, ctypes.c_int]
+        lib.oracle_adjoint_bc.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -179,19 +182,20 @@ class Oracle:
         return tu, tv
 
     def adjoint(self, u0, v0, params: dict, T: int, lu_T, lv_T, n_checkpoints: int = 0,
-                reaction: int = FHN, nthreads: int = 1):
+                reaction: int = FHN, nthreads: int = 1, boundary: int = PERIODIC):
         """Reverse-mode derivative of T steps of Eq. 1 (derivation in rdcnn_oracle.c).
 
         Returns (dL/du0, dL/dv0, grad) with grad = dL/d[Du, Dv, a, b, eps, c], given the
-        co-state (lu_T, lv_T) = dL/d(u_T, v_T).
+        co-state (lu_T, lv_T) = dL/d(u_T, v_T).  boundary: PERIODIC (the paper's torus) or
+        ZEROFLUX.
         """
         u0 = _plane(u0); v0 = _plane(v0); lu_T = _plane(lu_T); lv_T = _plane(lv_T)
         nn, nm = u0.shape
         lu0 = np.empty_like(u0); lv0 = np.empty_like(v0); g = np.zeros(6)
         p = pvec(params)
-        rc = self.lib.oracle_adjoint(nn, nm, _ptr(u0), _ptr(v0), _ptr(p), reaction, int(T), _ptr(lu_T),
-                                     _ptr(lv_T), int(n_checkpoints), _ptr(lu0), _ptr(lv0), _ptr(g),
-                                     nthreads)
+        rc = self.lib.oracle_adjoint_bc(nn, nm, _ptr(u0), _ptr(v0), _ptr(p), reaction, int(boundary), int(T),
+                                        _ptr(lu_T), _ptr(lv_T), int(n_checkpoints), _ptr(lu0), _ptr(lv0),
+                                        _ptr(g), nthreads)
         if rc != 0:
             raise RuntimeError("oracle_adjoint failed")
         return lu0, lv0, g
@@ -243,8 +247,8 @@ def scalar_map(u0: float, v0: float, params: dict, T: int):
 
 
 def adjoint(u0, v0, params: dict, T: int, lu_T, lv_T, n_checkpoints: int = 0,
-            reaction: int = FHN, nthreads: int = 1):
-    return _get().adjoint(u0, v0, params, T, lu_T, lv_T, n_checkpoints, reaction, nthreads)
+            reaction: int = FHN, nthreads: int = 1, boundary: int = PERIODIC):
+    return _get().adjoint(u0, v0, params, T, lu_T, lv_T, n_checkpoints, reaction, nthreads, boundary)
 
 
 # ---------------------------------------------------------------------------

@@ -112,11 +112,6 @@ static double laplacian_bc(const double *f, int64_t nn, int64_t nm, int64_t i, i
     return (vert + horz) - 4.0 * f[i * nm + j];
 }
 
-/* The toroidal Laplacian of the paper's model. */
-static double laplacian(const double *f, int64_t nn, int64_t nm, int64_t i, int64_t j) {
-    return laplacian_bc(f, nn, nm, i, j, ORACLE_PERIODIC);
-}
-
 /* Sum of the CeNN outputs y of the four neighbours of (i, j). */
 static double neighbour_output_sum(const double *x, int64_t nn, int64_t nm, int64_t i, int64_t j,
                                    int boundary) {
@@ -261,15 +256,24 @@ void oracle_scalar_map(double u0, double v0, const double *p, int64_t T,
  * grad[6] = dL/d{Du, Dv, a, b, eps, c}.
  * Forward states are rebuilt from checkpoints taken every S steps
  * (S = ceil(T / n_checkpoints), n_checkpoints <= 0 meaning ceil(sqrt(T))).
- * Returns 0, or -1 on bad sizes, a reaction other than FHN / NONE, or
- * allocation failure.  The boundary is always toroidal.
+ * Returns 0, or -1 on bad sizes, a reaction other than FHN / NONE, a bad
+ * boundary, or allocation failure.
+ *
+ * Zero flux (oracle_adjoint_bc with ORACLE_ZEROFLUX): the forward map uses
+ * the Laplacian whose missing neighbours are replaced by the cell itself.
+ * As a matrix, its off-diagonal entry (k, m) counts how often m is a
+ * neighbour of k, which is mutual, and the replaced neighbours only add to
+ * the diagonal, so it is symmetric as well.  The derivation above therefore
+ * holds word for word with Lap the zero-flux Laplacian, in the co-state
+ * update and in the Du / Dv sums.
  */
-int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
-                   const double *p, int reaction, int64_t T,
-                   const double *lu_T, const double *lv_T, int64_t n_checkpoints,
-                   double *lu0_out, double *lv0_out, double *grad, int nthreads) {
+int oracle_adjoint_bc(int64_t nn, int64_t nm, const double *u0, const double *v0,
+                      const double *p, int reaction, int boundary, int64_t T,
+                      const double *lu_T, const double *lv_T, int64_t n_checkpoints,
+                      double *lu0_out, double *lv0_out, double *grad, int nthreads) {
     if (nn <= 0 || nm <= 0 || T < 0) return -1;
     if (reaction != ORACLE_FHN && reaction != ORACLE_NONE) return -1;
+    if (boundary != ORACLE_PERIODIC && boundary != ORACLE_ZEROFLUX) return -1;
     const size_t n = (size_t)nn * (size_t)nm;
     for (int g = 0; g < 6; ++g) grad[g] = 0.0;
     memcpy(lu0_out, lu_T, n * sizeof(double));
@@ -300,7 +304,7 @@ int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
         memcpy(ck + (size_t)s * 2 * n, tmp_u, n * sizeof(double));
         memcpy(ck + (size_t)s * 2 * n + n, tmp_v, n * sizeof(double));
         const int64_t len = (s + 1) * S <= T ? S : T - s * S;
-        if (s + 1 < nseg) oracle_run(nn, nm, tmp_u, tmp_v, p, reaction, len, nthreads);
+        if (s + 1 < nseg) oracle_run_bc(nn, nm, tmp_u, tmp_v, p, reaction, boundary, len, nthreads);
     }
 
     memcpy(lu, lu_T, n * sizeof(double));
@@ -317,7 +321,7 @@ int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
         for (int64_t q = 1; q < len; ++q) {
             const double *pu = seg + (size_t)(q - 1) * 2 * n;
             double *qu = seg + (size_t)q * 2 * n;
-            oracle_step(nn, nm, pu, pu + n, qu, qu + n, p, reaction, nthreads);
+            oracle_step_bc(nn, nm, pu, pu + n, qu, qu + n, p, reaction, boundary, nthreads);
         }
         for (int64_t q = len - 1; q >= 0; --q) {
             const double *u = seg + (size_t)q * 2 * n;
@@ -327,8 +331,8 @@ int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
                 for (int64_t j = 0; j < nm; ++j) {
                     const int64_t k = i * nm + j;
                     const double uk = u[k], vk = v[k], luk = lu[k], lvk = lv[k];
-                    g[0] += luk * laplacian(u, nn, nm, i, j);
-                    g[1] += lvk * laplacian(v, nn, nm, i, j);
+                    g[0] += luk * laplacian_bc(u, nn, nm, i, j, boundary);
+                    g[1] += lvk * laplacian_bc(v, nn, nm, i, j, boundary);
                     if (fhn) {
                         g[2] += lvk * (-eps);
                         g[3] += lvk * (eps * vk);
@@ -349,8 +353,8 @@ int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
                         ru = (c - uk * uk) * luk - eps * lvk;
                         rv = -luk + eps * b * lvk;
                     }
-                    lun[k] = luk + dt * (ru + Du * laplacian(lu, nn, nm, i, j));
-                    lvn[k] = lvk + dt * (rv + Dv * laplacian(lv, nn, nm, i, j));
+                    lun[k] = luk + dt * (ru + Du * laplacian_bc(lu, nn, nm, i, j, boundary));
+                    lvn[k] = lvk + dt * (rv + Dv * laplacian_bc(lv, nn, nm, i, j, boundary));
                 }
             }
             double *t1 = lu, *t2 = lv;
@@ -361,4 +365,13 @@ int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
     memcpy(lv0_out, lv, n * sizeof(double));
     free(ck); free(seg); free(tmp_u); free(tmp_v); free(lu); free(lv); free(lun); free(lvn);
     return 0;
+}
+
+/* The toroidal adjoint (the paper's boundary). */
+int oracle_adjoint(int64_t nn, int64_t nm, const double *u0, const double *v0,
+                   const double *p, int reaction, int64_t T,
+                   const double *lu_T, const double *lv_T, int64_t n_checkpoints,
+                   double *lu0_out, double *lv0_out, double *grad, int nthreads) {
+    return oracle_adjoint_bc(nn, nm, u0, v0, p, reaction, ORACLE_PERIODIC, T, lu_T, lv_T, n_checkpoints,
+                             lu0_out, lv0_out, grad, nthreads);
 }

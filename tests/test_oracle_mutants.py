@@ -31,8 +31,12 @@ MUTANTS = {
     "adj_jac_uu": ("ru = (c - uk * uk) * luk", "ru = (c - 3.0 * uk * uk) * luk"),
     "adj_eps_sign": ("- eps * lvk;", "+ eps * lvk;"),
     "adj_grad_b": ("g[3] += lvk * (eps * vk);", "g[3] += lvk * vk;"),
-    "adj_grad_du_uses_v": ("g[0] += luk * laplacian(u,", "g[0] += luk * laplacian(v,"),
-    "adj_dv_term": ("rv + Dv * laplacian(lv", "rv + Du * laplacian(lv"),
+    "adj_grad_du_uses_v": ("g[0] += luk * laplacian_bc(u,", "g[0] += luk * laplacian_bc(v,"),
+    "adj_dv_term": ("rv + Dv * laplacian_bc(lv", "rv + Du * laplacian_bc(lv"),
+    "adj_zf_costate_on_torus": ("Du * laplacian_bc(lu, nn, nm, i, j, boundary)",
+                                "Du * laplacian_bc(lu, nn, nm, i, j, ORACLE_PERIODIC)"),
+    "adj_zf_grad_on_torus": ("g[1] += lvk * laplacian_bc(v, nn, nm, i, j, boundary);",
+                             "g[1] += lvk * laplacian_bc(v, nn, nm, i, j, ORACLE_PERIODIC);"),
     "zf_ghost_past_edge": ("return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);", "return i < 0 ? 1 : (i > n - 1 ? n - 2 : i);"),
     "zf_ignored": ("if (boundary == ORACLE_ZEROFLUX) return i < 0", "if (0) return i < 0"),
     "zf_columns_wrap": ("jm = neighbour_index(j - 1, nm, boundary);\n    double vert = f", "jm = wrap_index(j - 1, nm);\n    double vert = f"),

@@ -271,27 +271,36 @@ def _loss(u, v, wu, wv):
     return float(np.sum(wu * u) + np.sum(wv * v))
 
 
-@pytest.mark.parametrize("gene", [inp.default_params(), ODD_GENE], ids=["default", "odd"])
-def test_adjoint_matches_central_differences(oracle_mod, gene):
-    """Linear loss L = <wu, u_T> + <wv, v_T>; FD in every gene entry and along random directions."""
-    nn, nm, T = 7, 9, 25
+ADJ_CASES = [(inp.default_params(), "periodic", (7, 9)), (ODD_GENE, "periodic", (7, 9)),
+             (inp.default_params(), "zeroflux", (7, 9)), (ODD_GENE, "zeroflux", (2, 5))]
+
+
+@pytest.mark.parametrize("gene,boundary,shape", ADJ_CASES,
+                         ids=["default-torus", "odd-torus", "default-zeroflux", "odd-zeroflux-2x5"])
+def test_adjoint_matches_central_differences(oracle_mod, gene, boundary, shape):
+    """Linear loss L = <wu, u_T> + <wv, v_T>; FD of the forward map in every gene entry and
+    along random directions of the start state (the forward map is pinned on its own)."""
+    nn, nm = shape
+    T = 25
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
     x = inp.uniform_field(21, nn, nm)
     y = inp.uniform_field(22, nn, nm)
     wu = inp.uniform_field(23, nn, nm)
     wv = inp.uniform_field(24, nn, nm)
-    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=4)
+    run = lambda a, b, g: oracle_mod.run(a, b, g, T, boundary=bc)
+    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=4, boundary=bc)
     names = ["Du", "Dv", "a", "b", "eps", "c"]
     for k, name in enumerate(names):
         h = 1e-5 * max(1.0, abs(gene[name]))
         pp = dict(gene); pp[name] += h
         pm = dict(gene); pm[name] -= h
-        fd = (_loss(*oracle_mod.run(x, y, pp, T), wu, wv) - _loss(*oracle_mod.run(x, y, pm, T), wu, wv)) / (2 * h)
+        fd = (_loss(*run(x, y, pp), wu, wv) - _loss(*run(x, y, pm), wu, wv)) / (2 * h)
         assert abs(g[k] - fd) <= 1e-7 * max(1.0, abs(fd)), (name, g[k], fd)
     du = inp.uniform_field(25, nn, nm)
     dv = inp.uniform_field(26, nn, nm)
     h = 1e-5
-    fd = (_loss(*oracle_mod.run(x + h * du, y + h * dv, gene, T), wu, wv)
-          - _loss(*oracle_mod.run(x - h * du, y - h * dv, gene, T), wu, wv)) / (2 * h)
+    fd = (_loss(*run(x + h * du, y + h * dv, gene), wu, wv)
+          - _loss(*run(x - h * du, y - h * dv, gene), wu, wv)) / (2 * h)
     ad = float(np.sum(lu0 * du) + np.sum(lv0 * dv))
     assert abs(ad - fd) <= 1e-7 * max(1.0, abs(fd))
 
@@ -307,15 +316,18 @@ def test_adjoint_checkpoint_count_does_not_matter(oracle_mod):
         np.testing.assert_allclose(got[2], ref[2], rtol=1e-14, atol=1e-300)
 
 
-def test_adjoint_of_pure_diffusion_is_diffusion(oracle_mod):
-    """The periodic 5-point Laplacian is symmetric, so with no reaction the adjoint sweep is
-    the forward sweep applied to the co-state, and the gene gradients of the reaction vanish."""
+@pytest.mark.parametrize("boundary", ["periodic", "zeroflux"])
+def test_adjoint_of_pure_diffusion_is_diffusion(oracle_mod, boundary):
+    """The 5-point Laplacian is symmetric (on the torus, and under zero flux, where a missing
+    neighbour adds to the diagonal), so with no reaction the adjoint sweep is the forward
+    sweep applied to the co-state, and the gene gradients of the reaction vanish."""
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
     gene = ODD_GENE
     x = inp.uniform_field(41, 8, 11)
     wu = inp.uniform_field(42, 8, 11)
     wv = inp.uniform_field(43, 8, 11)
-    lu0, lv0, g = oracle_mod.adjoint(x, x, gene, 13, wu, wv, reaction=oracle_mod.NONE)
-    fu, fv = oracle_mod.run(wu, wv, gene, 13, reaction=oracle_mod.NONE)
+    lu0, lv0, g = oracle_mod.adjoint(x, x, gene, 13, wu, wv, reaction=oracle_mod.NONE, boundary=bc)
+    fu, fv = oracle_mod.run(wu, wv, gene, 13, reaction=oracle_mod.NONE, boundary=bc)
     assert np.array_equal(lu0, fu) and np.array_equal(lv0, fv)
     assert np.all(g[2:] == 0.0)
 
