@@ -4,7 +4,9 @@
 // one step (u+, v+) = F(u, v) and co-state (lu, lv) = dL/d(u+, v+):
 //   dL/du = lu + dt [ (c - u^2) lu - eps lv + Du Lap(lu) ]
 //   dL/dv = lv + dt [ -lu + eps b lv + Dv Lap(lv) ]
-// (the periodic 5-point Laplacian is symmetric, so it is its own transpose),
+// (the 5-point Laplacian is symmetric, so it is its own transpose: on the
+// torus, and under zero flux too, where a missing neighbour adds the cell
+// itself, i.e. to the diagonal, and adjacency stays mutual),
 // and the gene picks up, per step,
 //   dL/dDu += dt sum lu Lap(u)     dL/dDv += dt sum lv Lap(v)
 //   dL/dc  += dt sum lu u          dL/da  += dt sum lv (-eps)
@@ -12,7 +14,10 @@
 // with (u, v) the state before the step.  Because the Laplacian is symmetric,
 // sum lu Lap(u) = sum u Lap(lu): the Du / Dv terms reuse the co-state
 // neighbour sums the update forms anyway, and the state is needed only at
-// the centre cell.
+// the centre cell.  Under zero flux the co-state rows and columns beyond an
+// edge are mirrored exactly like the state's (the mirrored grid evolves as
+// the reflected image of the real one, forward and backward), so the
+// pipeline's mirrored halos serve both.
 //
 // Driver: a forward sweep stores n_ck checkpoints (every S = ceil(T/n_ck)
 // steps).  Segments are then processed last to first: k_forward_all rebuilds
@@ -71,7 +76,7 @@ __device__ __forceinline__ T warp_sum_t(T x) {
 // cp.async in the same commit groups as the co-state rows, kRing - 1 beats
 // ahead of use.  The six gene sums run in T over the owned cells and reach
 // FP64 once per warp (FP64 arithmetic is slow here).
-template <typename T, int K, int RX>
+template <typename T, int K, int RX, int BC>
 struct ReversePolicy {
     // A stage reads only its own ring slot of the beat and sums over owned
     // rows (q >= K, inside the light cone), so the fill may skip stages; the
@@ -85,7 +90,7 @@ struct ReversePolicy {
     T *__restrict__ lvn;
     int nn, nm;
     VT (*aux)[kRing][2][32];  // [stage][slot][field][lane]
-    int gi[K];                // next state row to copy, per stage
+    RowWalk<BC> gw[K];        // next state row to copy, per stage (wrapped / reflected)
     T rg[6];                  // sums: u Lap(lu), v Lap(lv), lv, lv v, lv (u - b v), lu u
 
     __device__ __forceinline__ void init() {
@@ -93,16 +98,16 @@ struct ReversePolicy {
         for (int q = 0; q < 6; ++q) rg[q] = T(0);
         // stage s at beat m reads input-row index q = m - s - 1
 #pragma unroll
-        for (int s = 0; s < K; ++s) gi[s] = wrap_row((int64_t)geo.r0 - K - s - 1, nn);
+        for (int s = 0; s < K; ++s) gw[s].start((int64_t)geo.r0 - K - s - 1, nn);
     }
     __device__ __forceinline__ void issue(int j) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            const int64_t off = (int64_t)gi[s] * nm + geo.lc;
+            const int64_t off = (int64_t)gw[s].g * nm + geo.lc;
             cp_async16(&aux[s][j % kRing][0][lane], state.u[s] + off);
             cp_async16(&aux[s][j % kRing][1][lane], state.v[s] + off);
-            gi[s] = (gi[s] + 1 == nn) ? 0 : gi[s] + 1;
+            gw[s].next(nn);
         }
     }
     __device__ __forceinline__ void begin_beat(int) {}
@@ -123,7 +128,10 @@ struct ReversePolicy {
                                                                e == V - 1 ? eu : B.u[e + 1]));
             const T sv = add_rn(add_rn(A.v[e], C.v[e]), add_rn(e == 0 ? wv : B.v[e - 1],
                                                                e == V - 1 ? ev : B.v[e + 1]));
-            const T uc = stu[e], vc = stv[e];
+            // a mirrored lane holds its state vector reversed, like its co-state
+            const bool flip = (BC == BC_MIRROR) && geo.rev;
+            const T uc = flip ? stu[V - 1 - e] : stu[e];
+            const T vc = flip ? stv[V - 1 - e] : stv[e];
             // co-state update with the centre term folded in, like the forward:
             //   lu + dt [ Du s(lu) + (c - 4 Du - u^2) lu - eps lv ]
             //   lv + dt [ Dv s(lv) + (eps b - 4 Dv) lv - lu ]
@@ -176,7 +184,7 @@ struct ReversePolicy {
 // K reverse steps: co-state (lu, lv) at t_hi -> (lun, lvn) at t_hi - K, with
 // state.u[s], state.v[s] = state at t_hi - s - 1.  H: halo lanes (fixed per
 // call sequence so every launch has the same warp -> cells map).
-template <typename T, int K, int H, int RX>
+template <typename T, int K, int H, int RX, int BC>
 __global__ void __launch_bounds__(kPipeBlock)
 k_adjoint_pipe(const T *__restrict__ lu, const T *__restrict__ lv, T *__restrict__ lun,
                T *__restrict__ lvn, StagePlanes<T> state, double *__restrict__ partial, int nn,
@@ -184,30 +192,30 @@ k_adjoint_pipe(const T *__restrict__ lu, const T *__restrict__ lv, T *__restrict
     pdl_wait();
     const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
     if (wid >= nwarps) return;
-    const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
+    const StripGeom geo = strip_geom<T, K, H, BC>(wid % bands, wid / bands, nn, nm, rows);
     typedef typename Vec<T>::type VT;
     // state rings in dynamic shared memory: [warp][stage][slot][field][lane]
     extern __shared__ __align__(16) unsigned char adj_dyn_smem[];
     VT(*aux_mem)[K][kRing][2][32] = reinterpret_cast<VT(*)[K][kRing][2][32]>(adj_dyn_smem);
-    ReversePolicy<T, K, RX> pol{p, geo, state, lun, lvn, nn, nm, aux_mem[(threadIdx.x >> 5) % kTemporalWarps]};
+    ReversePolicy<T, K, RX, BC> pol{p, geo, state, lun, lvn, nn, nm, aux_mem[(threadIdx.x >> 5) % kTemporalWarps]};
     pol.init();
-    pipeline_strip<T, K>(geo, lu, lv, nn, nm, pol);
+    pipeline_strip<T, K, BC>(geo, lu, lv, nn, nm, pol);
     pol.flush(partial + (int64_t)wid * 6);
     pdl_trigger();
 }
 
 // K forward steps from (u, v), storing the state after every step s+1 into
 // planes.u[s], planes.v[s] (the states a reverse sweep reads).
-template <typename T, int K, int H, int RX>
+template <typename T, int K, int H, int RX, int BC>
 __global__ void __launch_bounds__(kPipeBlock)
 k_forward_all(const T *__restrict__ u, const T *__restrict__ v, StagePlanes<T> planes, int nn,
               int nm, int bands, int nwarps, int rows, Coef<T> p) {
     pdl_wait();
     const int wid = blockIdx.x * kTemporalWarps + (threadIdx.x >> 5);
     if (wid >= nwarps) return;
-    const StripGeom geo = strip_geom<T, K, H>(wid % bands, wid / bands, nn, nm, rows);
+    const StripGeom geo = strip_geom<T, K, H, BC>(wid % bands, wid / bands, nn, nm, rows);
     ForwardAllPolicy<T, K, RX> pol{p, geo, planes, nm};
-    pipeline_strip<T, K>(geo, u, v, nn, nm, pol);
+    pipeline_strip<T, K, BC>(geo, u, v, nn, nm, pol);
     pdl_trigger();
 }
 
@@ -259,70 +267,85 @@ constexpr size_t pipe_smem_bytes() {
 }
 
 // Opt the kernel in to its dynamic shared memory (above the 48 KB default), once.
-template <typename T, int K, int RX>
+template <typename T, int K, int RX, int BC>
 cudaError_t pipe_smem_optin() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady)
-        done = cudaFuncSetAttribute(k_adjoint_pipe<T, K, 1, RX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        done = cudaFuncSetAttribute(k_adjoint_pipe<T, K, 1, RX, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)pipe_smem_bytes<T, K>());
     return done;
 }
 
+// Dispatch of the adjoint's models: FitzHugh-Nagumo or no reaction, torus or
+// zero flux, as compile-time tags f(IntC<RX>{}, IntC<BC>{}).
+template <class F>
+cudaError_t with_adj_model(int reaction, int boundary, F &&f) {
+    const bool zf = (boundary == RDCNN_BC_ZEROFLUX);
+    if (reaction == RDCNN_REACTION_FHN)
+        return zf ? f(IntC<RX_FHN>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_FHN>{}, IntC<BC_WRAP>{});
+    if (reaction == RDCNN_REACTION_NONE)
+        return zf ? f(IntC<RX_NONE>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_NONE>{}, IntC<BC_WRAP>{});
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int K>
-cudaError_t reverse_launch_k(int reaction, const void *lu, const void *lv, void *lun, void *lvn,
+cudaError_t reverse_launch_k(int reaction, int boundary, const void *lu, const void *lv, void *lun, void *lvn,
                              const StagePlanes<T> &st, double *partial, int64_t nn, int64_t nm,
                              const PipeShape &sh, const rdcnn_params &p, cudaStream_t s) {
     const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const AdjCoef<T> c = make_adj_coef<T>(p, reaction);
     const size_t smem = pipe_smem_bytes<T, K>();
-    const cudaError_t oe = reaction == RDCNN_REACTION_FHN ? pipe_smem_optin<T, K, RX_FHN>()
-                                                          : pipe_smem_optin<T, K, RX_NONE>();
-    if (oe != cudaSuccess) return oe;
-    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_adjoint_pipe<T, K, 1, RX_FHN>
-                                                                 : k_adjoint_pipe<T, K, 1, RX_NONE>,
-                                   grid, kPipeBlock, smem, s, (const T *)lu, (const T *)lv, (T *)lun, (T *)lvn,
-                                   st, partial, (int)nn, (int)nm, sh.bands, sh.nwarps, sh.rows, c);
-    count_launches(1);
-    return e;
+    return with_adj_model(reaction, boundary, [&](auto rx, auto bc) {
+        constexpr int RX = decltype(rx)::value;
+        constexpr int BC = decltype(bc)::value;
+        const cudaError_t oe = pipe_smem_optin<T, K, RX, BC>();
+        if (oe != cudaSuccess) return oe;
+        const cudaError_t e = launch_k(k_adjoint_pipe<T, K, 1, RX, BC>, grid, kPipeBlock, smem, s, (const T *)lu,
+                                       (const T *)lv, (T *)lun, (T *)lvn, st, partial, (int)nn, (int)nm,
+                                       sh.bands, sh.nwarps, sh.rows, c);
+        count_launches(1);
+        return e;
+    });
 }
 
 template <typename T, int K>
-cudaError_t forward_all_launch_k(int reaction, const void *u, const void *v, const StagePlanes<T> &pl,
-                                 int64_t nn, int64_t nm, const PipeShape &sh, const rdcnn_params &p,
-                                 cudaStream_t s) {
+cudaError_t forward_all_launch_k(int reaction, int boundary, const void *u, const void *v,
+                                 const StagePlanes<T> &pl, int64_t nn, int64_t nm, const PipeShape &sh,
+                                 const rdcnn_params &p, cudaStream_t s) {
     const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const Coef<T> c = make_coef<T>(p, reaction);
-    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_forward_all<T, K, 1, RX_FHN>
-                                                                 : k_forward_all<T, K, 1, RX_NONE>,
-                                   grid, kPipeBlock, 0, s, (const T *)u, (const T *)v, pl, (int)nn, (int)nm,
-                                   sh.bands, sh.nwarps, sh.rows, c);
-    count_launches(1);
-    return e;
+    return with_adj_model(reaction, boundary, [&](auto rx, auto bc) {
+        const cudaError_t e = launch_k(k_forward_all<T, K, 1, decltype(rx)::value, decltype(bc)::value>, grid,
+                                       kPipeBlock, 0, s, (const T *)u, (const T *)v, pl, (int)nn, (int)nm,
+                                       sh.bands, sh.nwarps, sh.rows, c);
+        count_launches(1);
+        return e;
+    });
 }
 
 // Depth dispatch (depth <= V keeps one halo lane): F32 1..4, F64 1..2.
 template <typename T>
-cudaError_t reverse_launch(int reaction, int k, const void *lu, const void *lv, void *lun, void *lvn,
-                           const StagePlanes<T> &st, double *partial, int64_t nn, int64_t nm,
+cudaError_t reverse_launch(int reaction, int boundary, int k, const void *lu, const void *lv, void *lun,
+                           void *lvn, const StagePlanes<T> &st, double *partial, int64_t nn, int64_t nm,
                            const PipeShape &sh, const rdcnn_params &p, cudaStream_t s) {
     switch (k) {
-        case 1: return reverse_launch_k<T, 1>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
-        case 2: return reverse_launch_k<T, 2>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
-        case 3: if constexpr (Vec<T>::N >= 3) return reverse_launch_k<T, 3>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
-        case 4: if constexpr (Vec<T>::N >= 4) return reverse_launch_k<T, 4>(reaction, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
+        case 1: return reverse_launch_k<T, 1>(reaction, boundary, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
+        case 2: return reverse_launch_k<T, 2>(reaction, boundary, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s);
+        case 3: if constexpr (Vec<T>::N >= 3) return reverse_launch_k<T, 3>(reaction, boundary, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
+        case 4: if constexpr (Vec<T>::N >= 4) return reverse_launch_k<T, 4>(reaction, boundary, lu, lv, lun, lvn, st, partial, nn, nm, sh, p, s); break;
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t forward_all_launch(int reaction, int k, const void *u, const void *v, const StagePlanes<T> &pl,
+cudaError_t forward_all_launch(int reaction, int boundary, int k, const void *u, const void *v, const StagePlanes<T> &pl,
                                int64_t nn, int64_t nm, const PipeShape &sh, const rdcnn_params &p,
                                cudaStream_t s) {
     switch (k) {
-        case 1: return forward_all_launch_k<T, 1>(reaction, u, v, pl, nn, nm, sh, p, s);
-        case 2: return forward_all_launch_k<T, 2>(reaction, u, v, pl, nn, nm, sh, p, s);
-        case 3: if constexpr (Vec<T>::N >= 3) return forward_all_launch_k<T, 3>(reaction, u, v, pl, nn, nm, sh, p, s); break;
-        case 4: if constexpr (Vec<T>::N >= 4) return forward_all_launch_k<T, 4>(reaction, u, v, pl, nn, nm, sh, p, s); break;
+        case 1: return forward_all_launch_k<T, 1>(reaction, boundary, u, v, pl, nn, nm, sh, p, s);
+        case 2: return forward_all_launch_k<T, 2>(reaction, boundary, u, v, pl, nn, nm, sh, p, s);
+        case 3: if constexpr (Vec<T>::N >= 3) return forward_all_launch_k<T, 3>(reaction, boundary, u, v, pl, nn, nm, sh, p, s); break;
+        case 4: if constexpr (Vec<T>::N >= 4) return forward_all_launch_k<T, 4>(reaction, boundary, u, v, pl, nn, nm, sh, p, s); break;
     }
     return cudaErrorInvalidValue;
 }
@@ -351,7 +374,7 @@ AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck) 
 }
 
 template <typename T>
-int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, cudaStream_t s,
+int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary, cudaStream_t s,
               int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T, const void *dLdv_T,
               const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
     const size_t bytes = (size_t)nn * nm * sizeof(T);
@@ -383,7 +406,7 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             const int kk = (int)std::min<int64_t>(kf, len - j * kf);
             void *nu = (j == nl - 1) ? (void *)ck_u(i + 1) : (void *)seg_u(j % 2);
             void *nv = (j == nl - 1) ? (void *)ck_v(i + 1) : (void *)seg_v(j % 2);
-            e = launch_temporal(dtype, reaction, RDCNN_BC_PERIODIC, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
+            e = launch_temporal(dtype, reaction, boundary, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
             if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
             cu = nu; cv = nv;
         }
@@ -398,7 +421,7 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             const int kk = (int)std::min<int64_t>(ka, len - 1 - q);
             StagePlanes<T> pl{};
             for (int j = 0; j < kk; ++j) { pl.u[j] = seg_u(q + 1 + j); pl.v[j] = seg_v(q + 1 + j); }
-            e = forward_all_launch<T>(reaction, kk, state_u(q), state_v(q), pl, nn, nm, sh, p, s);
+            e = forward_all_launch<T>(reaction, boundary, kk, state_u(q), state_v(q), pl, nn, nm, sh, p, s);
             if (e != cudaSuccess) return cuda_error(e, "adjoint recompute");
             q += kk;
         }
@@ -406,7 +429,7 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             const int kk = (int)std::min<int64_t>(ka, qh);
             StagePlanes<T> st{};
             for (int j = 0; j < kk; ++j) { st.u[j] = state_u(qh - 1 - j); st.v[j] = state_v(qh - 1 - j); }
-            e = reverse_launch<T>(reaction, kk, lam_u[cur], lam_v[cur], lam_u[cur ^ 1], lam_v[cur ^ 1], st,
+            e = reverse_launch<T>(reaction, boundary, kk, lam_u[cur], lam_v[cur], lam_u[cur ^ 1], lam_v[cur ^ 1], st,
                                   partial, nn, nm, sh, p, s);
             if (e != cudaSuccess) return cuda_error(e, "adjoint reverse step");
             cur ^= 1;
@@ -453,8 +476,8 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
-    if (boundary != RDCNN_BC_PERIODIC || reaction == RDCNN_REACTION_CENN)
-        return set_error(RDCNN_EINVAL, "the adjoint supports the periodic FHN / NONE models only");
+    if (reaction == RDCNN_REACTION_CENN)
+        return set_error(RDCNN_EINVAL, "the adjoint supports the FHN / NONE models only");
     if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
@@ -468,9 +491,9 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     if (workspace_bytes < L.total)
         return set_error(RDCNN_ESPACE, "adjoint workspace has %zu bytes, need %zu", workspace_bytes, L.total);
     if (dtype == RDCNN_F64)
-        return adjoint_t<double>(nn, nm, p, dtype, reaction, s, T, u0, v0, dLdu_T, dLdv_T, L,
+        return adjoint_t<double>(nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
                                  (char *)workspace, dLdu0, dLdv0, grad);
-    return adjoint_t<float>(nn, nm, p, dtype, reaction, s, T, u0, v0, dLdu_T, dLdv_T, L,
+    return adjoint_t<float>(nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
                             (char *)workspace, dLdu0, dLdv0, grad);
 }
 

@@ -166,3 +166,78 @@ def test_autograd_end_to_end_fit_step(rd):
         th2 = theta - 1e-3 * theta.grad / theta.grad.norm()
     u2, _ = rd.RDCNNFunction.apply(x, x, th2, T, p["dt"])
     assert torch.mean((u2 - target) ** 2).item() < loss.item()
+
+
+# ----------------------------------------------------------------------------- zero-flux boundary
+
+ZF_SHAPES = [(24, 40), (9, 6), (33, 130), (1, 8)]
+
+
+@pytest.mark.parametrize("shape", ZF_SHAPES, ids=[f"{a}x{b}" for a, b in ZF_SHAPES])
+@pytest.mark.parametrize("nck", [0, 7])
+def test_f64_zeroflux_adjoint_matches_oracle(rd, oracle_mod, shape, nck):
+    """Zero flux: mirrored halos for the co-state and for the state rows the reverse pass
+    reads; the oracle adjoint (pinned to central differences of the zero-flux forward)."""
+    nn, nm = shape
+    T = 37
+    params = inp.default_params(Du=0.17, Dv=0.4)
+    x = inp.uniform_field(61, nn, nm)
+    y = inp.uniform_field(62, nn, nm)
+    wu = inp.uniform_field(63, nn, nm)
+    wv = inp.uniform_field(64, nn, nm)
+    g = rd.Grid(nn, nm, params, dtype=F64, boundary="zeroflux")
+    du, dv, gp = g.adjoint(T, _dev(x, F64), _dev(y, F64), _dev(wu, F64), _dev(wv, F64), nck)
+    torch.cuda.synchronize()
+    ou, ov, og = oracle_mod.adjoint(x, y, params, T, wu, wv, n_checkpoints=nck, boundary=oracle_mod.ZEROFLUX)
+    assert normwise(du.cpu().numpy(), ou) < 1e-10 and normwise(dv.cpu().numpy(), ov) < 1e-10
+    np.testing.assert_allclose(np.array([gp[k] for k in NAMES]), og, rtol=1e-9, atol=1e-12)
+
+
+def test_f32_zeroflux_adjoint_short_horizon(rd, oracle_mod):
+    N, T = 200, 20
+    params = inp.default_params()
+    x = f32(inp.uniform_field(65, N, N))
+    gu = f32(inp.uniform_field(66, N, N)) / (N * N)
+    gv = f32(inp.uniform_field(67, N, N)) / (N * N)
+    g = rd.Grid(N, N, params, dtype=F32, boundary="zeroflux")
+    du, dv, gp = g.adjoint(T, _dev(x, F32), _dev(x, F32), _dev(gu, F32), _dev(gv, F32))
+    torch.cuda.synchronize()
+    ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, gv, boundary=oracle_mod.ZEROFLUX)
+    assert normwise(du.double().cpu().numpy(), ou) <= 1e-5 and normwise(dv.double().cpu().numpy(), ov) <= 1e-5
+    got = np.array([gp[k] for k in NAMES])
+    np.testing.assert_allclose(got, og, rtol=1e-5, atol=1e-6 * np.linalg.norm(og))
+
+
+def test_zeroflux_adjoint_without_reaction_is_forward_of_costate(rd):
+    """The zero-flux Laplacian is symmetric too: with no reaction the adjoint sweep equals
+    the zero-flux forward sweep of the co-state, bit for bit."""
+    nn, nm, T = 32, 64, 21
+    params = inp.default_params(Du=0.13, Dv=0.21)
+    x = f32(inp.uniform_field(68, nn, nm))
+    wu = f32(inp.uniform_field(69, nn, nm))
+    wv = f32(inp.uniform_field(70, nn, nm))
+    g = rd.Grid(nn, nm, params, dtype=F32, reaction="none", boundary="zeroflux")
+    du, dv, gp = g.adjoint(T, _dev(x, F32), _dev(x, F32), _dev(wu, F32), _dev(wv, F32))
+    fu, fv = gpu_run(rd, wu, wv, params, T, F32, "step1", reaction="none", boundary="zeroflux")
+    assert np.array_equal(du.double().cpu().numpy(), fu) and np.array_equal(dv.double().cpu().numpy(), fv)
+    assert all(gp[k] == 0.0 for k in ("a", "b", "eps", "c"))
+
+
+def test_zeroflux_autograd_gradcheck_f64(rd):
+    from torch.autograd import gradcheck
+
+    nn, nm, T = 6, 8, 5
+    u0 = _dev(inp.uniform_field(71, nn, nm), F64).requires_grad_()
+    v0 = _dev(inp.uniform_field(72, nn, nm), F64).requires_grad_()
+    p = inp.default_params()
+    theta = torch.tensor([p[k] for k in NAMES], dtype=F64, device="cuda", requires_grad=True)
+    f = lambda a, b, t: rd.RDCNNFunction.apply(a, b, t, T, p["dt"], 0, "zeroflux")  # noqa: E731
+    assert gradcheck(f, (u0, v0, theta), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_cenn_adjoint_rejected(rd):
+    gene = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.2, "Du": 0.1, "Dv": 0.0}
+    g = rd.Grid(8, 8, gene, dtype=F32, reaction="cenn")
+    z = torch.zeros((8, 8), dtype=F32, device="cuda")
+    with pytest.raises(rd.RDCNNError):
+        g.adjoint(3, z, z, z, z)
