@@ -245,11 +245,14 @@ typedef struct rdcnn_instance {
 int rdcnn_batch_workspace_bytes(const rdcnn_instance *inst, int n, int dtype,
                                 const rdcnn_tune *tune, size_t *bytes);
 
-/* Run T steps of Eq. 1 on all n instances with the same reaction and dtype.
+/* Run T steps of Eq. 1 on all n instances with the same reaction and dtype
+ * (RDCNN_F32, F64, BF16 or F16; 16-bit planes compute in FP32 and round the
+ * state once per launch, as rdcnn_run's TEMPORAL variant does).
  * All instances advance together: each launch covers every instance for k
  * steps, so small grids do not pay one launch per step each.  Vectorised
- * layout rules as for rdcnn_run apply to every instance (NM multiple of
- * 4 / 2, 16-byte aligned pointers), else RDCNN_EINVAL.  tune may be NULL.
+ * layout rules as for rdcnn_run apply to every instance (NM a multiple of 4,
+ * or 2 for F64; 16-byte aligned pointers, 8-byte for BF16 / F16), else
+ * RDCNN_EINVAL.  tune may be NULL.
  * Asynchronous on `stream`, except that the work table is copied to the
  * device first (host-synchronous copy into `workspace`). */
 int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction,
@@ -258,10 +261,9 @@ int rdcnn_batch_run(const rdcnn_instance *inst, int n, int64_t T, int dtype, int
 
 /* rdcnn_batch_run with the model variants: boundary RDCNN_BC_PERIODIC or
  * RDCNN_BC_ZEROFLUX, reaction FHN / NONE / CENN (the CeNN gene may carry
- * feedback weights of either sign), shared by all instances.  FP32 supports
- * every combination; FP64 the periodic FHN / NONE ones (RDCNN_EINVAL
- * otherwise).  rdcnn_batch_run(...) == rdcnn_batch_run_model(...,
- * RDCNN_BC_PERIODIC, ...). */
+ * feedback weights of either sign), shared by all instances; every dtype
+ * supports every combination.  rdcnn_batch_run(...) ==
+ * rdcnn_batch_run_model(..., RDCNN_BC_PERIODIC, ...). */
 int rdcnn_batch_run_model(const rdcnn_instance *inst, int n, int64_t T, int dtype, int reaction,
                           int boundary, const rdcnn_tune *tune, void *workspace, size_t workspace_bytes,
                           void *stream);
@@ -274,7 +276,8 @@ int rdcnn_batch_run_model(const rdcnn_instance *inst, int n, int64_t T, int dtyp
  *   mean(u), var(u), min(u), max(u), mean(v), var(v),
  *   mean of |u(i+1,j) - u(i,j)| + |u(i,j+1) - u(i,j)| (wrapping), and the
  *   fraction of cells where that sum exceeds `threshold`.
- * Variances are population variances.  Work runs on `stream`; the call
+ * Variances are population variances.  dtype: any RDCNN_* plane type (16-bit
+ * planes are read into FP32).  Work runs on `stream`; the call
  * returns when `out` is filled.  workspace: device, at least
  * rdcnn_summary_workspace_bytes.  Errors: RDCNN_EINVAL, RDCNN_ESPACE,
  * RDCNN_ECUDA. */

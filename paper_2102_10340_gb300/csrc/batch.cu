@@ -22,12 +22,16 @@
 #include "temporal.cuh"
 #include "batch_kernels.cuh"
 
-// the kernels compile in batch_f32a.cu .. batch_f32c.cu and batch_f64.cu
-RDK_EXTERN_BATCH(float, 1, 1) RDK_EXTERN_BATCH(float, 2, 1) RDK_EXTERN_BATCH(float, 3, 1)
-RDK_EXTERN_BATCH(float, 4, 1)
-RDK_EXTERN_BATCH(float, 1, 2) RDK_EXTERN_BATCH(float, 2, 2) RDK_EXTERN_BATCH(float, 3, 2)
-RDK_EXTERN_BATCH(float, 4, 2) RDK_EXTERN_BATCH(float, 5, 2) RDK_EXTERN_BATCH(float, 6, 2)
-RDK_EXTERN_BATCH(float, 7, 2) RDK_EXTERN_BATCH(float, 8, 2)
+// the kernels compile in batch_f32a.cu .. batch_f32c.cu, batch_f64.cu,
+// batch_bf16a.cu .. batch_bf16c.cu and batch_f16a.cu .. batch_f16c.cu
+#define RDK_EXTERN_BATCH_32(TT)                                                                  \
+    RDK_EXTERN_BATCH(TT, 1, 1) RDK_EXTERN_BATCH(TT, 2, 1) RDK_EXTERN_BATCH(TT, 3, 1)            \
+    RDK_EXTERN_BATCH(TT, 4, 1) RDK_EXTERN_BATCH(TT, 1, 2) RDK_EXTERN_BATCH(TT, 2, 2)            \
+    RDK_EXTERN_BATCH(TT, 3, 2) RDK_EXTERN_BATCH(TT, 4, 2) RDK_EXTERN_BATCH(TT, 5, 2)            \
+    RDK_EXTERN_BATCH(TT, 6, 2) RDK_EXTERN_BATCH(TT, 7, 2) RDK_EXTERN_BATCH(TT, 8, 2)
+RDK_EXTERN_BATCH_32(float)
+RDK_EXTERN_BATCH_32(__nv_bfloat16)
+RDK_EXTERN_BATCH_32(__half)
 RDK_EXTERN_BATCH(double, 1, 1) RDK_EXTERN_BATCH(double, 2, 1)
 RDK_EXTERN_BATCH(double, 1, 2) RDK_EXTERN_BATCH(double, 2, 2) RDK_EXTERN_BATCH(double, 3, 2)
 RDK_EXTERN_BATCH(double, 4, 2)
@@ -53,12 +57,11 @@ cudaError_t batch_launch_h(int reaction, int boundary, int k, const BatchDesc *t
 
 cudaError_t batch_launch(int dtype, int reaction, int boundary, int k, int H, const BatchDesc *tab, int n,
                          long long nwarps, int flip, cudaStream_t s) {
-    if (dtype == RDCNN_F64) {
-        if (H == 1) return batch_launch_h<double, 1>(reaction, boundary, k, tab, n, nwarps, flip, s);
-        return batch_launch_h<double, 2>(reaction, boundary, k, tab, n, nwarps, flip, s);
-    }
-    if (H == 1) return batch_launch_h<float, 1>(reaction, boundary, k, tab, n, nwarps, flip, s);
-    return batch_launch_h<float, 2>(reaction, boundary, k, tab, n, nwarps, flip, s);
+    return with_dtype(dtype, [&](auto tag) {
+        using T = decltype(tag);
+        if (H == 1) return batch_launch_h<T, 1>(reaction, boundary, k, tab, n, nwarps, flip, s);
+        return batch_launch_h<T, 2>(reaction, boundary, k, tab, n, nwarps, flip, s);
+    });
 }
 
 int batch_default_rows(int64_t nn) { return nn >= 1024 ? 64 : 32; }
@@ -82,14 +85,13 @@ std::vector<int> plan_depths(int64_t T, int k) {
 
 int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, int boundary, int *warn) {
     if (!inst || n < 1) return set_error(RDCNN_EINVAL, "need at least one instance");
-    if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "bad dtype");
+    if (dtype != RDCNN_F32 && dtype != RDCNN_F64 && !is_16bit(dtype)) return set_error(RDCNN_EINVAL, "bad dtype");
     if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE && reaction != RDCNN_REACTION_CENN)
         return set_error(RDCNN_EINVAL, "bad reaction");
     if (boundary != RDCNN_BC_PERIODIC && boundary != RDCNN_BC_ZEROFLUX)
         return set_error(RDCNN_EINVAL, "bad boundary");
-    if (dtype == RDCNN_F64 && (reaction == RDCNN_REACTION_CENN || boundary != RDCNN_BC_PERIODIC))
-        return set_error(RDCNN_EINVAL, "the FP64 batch supports the periodic FHN / NONE models only");
     const int V = vec_width(dtype);
+    const size_t align = vec_align(dtype);
     *warn = RDCNN_OK;
     for (int i = 0; i < n; ++i) {
         const rdcnn_instance &x = inst[i];
@@ -99,8 +101,9 @@ int validate_batch(const rdcnn_instance *inst, int n, int dtype, int reaction, i
             return set_error(RDCNN_EINVAL, "instance %d: NM must be a multiple of %d", i, V);
         if (!x.u || !x.v || !x.su || !x.sv)
             return set_error(RDCNN_EINVAL, "instance %d: NULL plane", i);
-        if (!aligned16(x.u) || !aligned16(x.v) || !aligned16(x.su) || !aligned16(x.sv))
-            return set_error(RDCNN_EINVAL, "instance %d: planes must be 16-byte aligned", i);
+        if (!aligned_to(x.u, align) || !aligned_to(x.v, align) || !aligned_to(x.su, align) ||
+            !aligned_to(x.sv, align))
+            return set_error(RDCNN_EINVAL, "instance %d: planes must be %zu-byte aligned", i, align);
         const int pc = check_params(&x.params, reaction);
         if (pc < 0) {
             char why[256];

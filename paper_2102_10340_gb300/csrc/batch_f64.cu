@@ -1,5 +1,5 @@
 // batch_f64.cu -- batched temporal launchers, FP64 (depths 1-2 with one halo
-// lane, 1-4 with two; periodic FitzHugh-Nagumo / pure diffusion).
+// lane, 1-4 with two).
 #include "batch_kernels.cuh"
 
 RDK_INSTANTIATE_BATCH(double, 1, 1)

@@ -39,9 +39,10 @@ k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int
     const BatchDesc &d = tab[lo];
     const int local = (int)(wid - d.warp_begin);
     const int bands = d.bands;
-    Coef<T> p;
-    p.dt = T(d.dt); p.Du = T(d.Du); p.Dv = T(d.Dv); p.cm4 = T(d.cm4);
-    p.mthird = T(d.mthird); p.meps = T(d.meps); p.ebm4 = T(d.ebm4); p.mepsa = T(d.mepsa);
+    typedef CT<T> C;  // arithmetic type (FP32 for 16-bit planes)
+    Coef<C> p;
+    p.dt = C(d.dt); p.Du = C(d.Du); p.Dv = C(d.Dv); p.cm4 = C(d.cm4);
+    p.mthird = C(d.mthird); p.meps = C(d.meps); p.ebm4 = C(d.ebm4); p.mepsa = C(d.mepsa);
     const T *su = (const T *)(flip ? d.su : d.u);
     const T *sv = (const T *)(flip ? d.sv : d.v);
     T *du = (T *)(flip ? d.u : d.su);
@@ -50,29 +51,19 @@ k_batch_temporal(const BatchDesc *__restrict__ tab, int n, long long nwarps, int
     pdl_trigger();
 }
 
-// One depth.  FP32: every model of the single-grid kernels; FP64: the
-// periodic FitzHugh-Nagumo / pure-diffusion pair (the caller checks).
+// One depth, every model of the single-grid kernels (T = float, double,
+// __nv_bfloat16 or __half planes; 16-bit planes round once per launch).
 template <typename T, int K, int H>
 cudaError_t batch_launch_khr(int reaction, int boundary, const BatchDesc *tab, int n, long long nwarps,
                              int flip, cudaStream_t s) {
     const int wpb = kBatchBlock / 32;
     const unsigned grid = (unsigned)((nwarps + wpb - 1) / wpb);
-    if constexpr (std::is_same<T, double>::value) {
-        if (boundary != RDCNN_BC_PERIODIC) return cudaErrorInvalidValue;
-        if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE) return cudaErrorInvalidValue;
-        const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_batch_temporal<T, K, H, RX_FHN, BC_WRAP>
-                                                                      : k_batch_temporal<T, K, H, RX_NONE, BC_WRAP>,
+    return with_model(reaction, boundary, [&](auto rx, auto bc) {
+        const cudaError_t e = launch_k(k_batch_temporal<T, K, H, decltype(rx)::value, decltype(bc)::value>,
                                        grid, kBatchBlock, 0, s, tab, n, nwarps, flip);
         count_launches(1);
         return e;
-    } else {
-        return with_model(reaction, boundary, [&](auto rx, auto bc) {
-            const cudaError_t e = launch_k(k_batch_temporal<T, K, H, decltype(rx)::value, decltype(bc)::value>,
-                                           grid, kBatchBlock, 0, s, tab, n, nwarps, flip);
-            count_launches(1);
-            return e;
-        });
-    }
+    });
 }
 
 }  // namespace rdk

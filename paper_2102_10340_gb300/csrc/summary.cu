@@ -12,7 +12,8 @@
 // (population variance; differences wrap around the torus).
 //
 // Pass 1 (k_summary_partial): each block takes a fixed row range of one
-// instance (a warp per row), sums in T within each warp and combines the
+// instance (a warp per row), sums in T (FP32 for FP32 and 16-bit planes,
+// FP64 for FP64 planes) within each warp and combines the
 // warps in FP64 into one partial record.  Pass 2 (k_summary_final): one block per
 // instance sums its partial records in a fixed order.  The result does not
 // depend on timing (no atomics).
@@ -36,8 +37,18 @@ struct SumDesc {
     int nn, nm;
     long long block_begin;  // first partial-record index of this instance
     int nblocks;
-    int dtype64;            // 1: planes hold doubles
+    int dtype;              // RDCNN_F32 / F64 / BF16 / F16: the planes' element type
 };
+
+// Element 0 of a plane of the given element type, as a double.
+__device__ __forceinline__ double first_value(const void *p, int dtype) {
+    switch (dtype) {
+        case RDCNN_F64: return load1((const double *)p);
+        case RDCNN_BF16: return (double)load1((const __nv_bfloat16 *)p);
+        case RDCNN_F16: return (double)load1((const __half *)p);
+        default: return (double)load1((const float *)p);
+    }
+}
 
 // Partial record: sums of (u - u0), (u - u0)^2, (v - v0), (v - v0)^2, |grad u|,
 // edge count, and min / max of u (u0, v0: the instance's first cell).
@@ -63,10 +74,12 @@ __device__ __forceinline__ T warp_red_max(T x) {
 
 // Pass 1: block b covers kSumRowsPerBlock rows of one instance, one warp per
 // row, lanes striding the columns (coalesced loads, no index division).  Each
-// lane sums in T; warps reduce in T; the block combines its warps in FP64.
-template <typename T>
+// lane sums in T = CT<S> (S: the plane's storage type); warps reduce in T;
+// the block combines its warps in FP64.
+template <typename S>
 __global__ void __launch_bounds__(kSumBlock)
-k_summary_partial(const SumDesc *__restrict__ tab, int n, T threshold, Partial *__restrict__ part) {
+k_summary_partial(const SumDesc *__restrict__ tab, int n, CT<S> threshold, Partial *__restrict__ part) {
+    typedef CT<S> T;
     __shared__ double sh[kSumBlock / 32][kFields];
     const long long b = blockIdx.x;
     int lo = 0, hi = n - 1;
@@ -75,25 +88,25 @@ k_summary_partial(const SumDesc *__restrict__ tab, int n, T threshold, Partial *
         if (tab[mid].block_begin <= b) lo = mid; else hi = mid - 1;
     }
     const SumDesc d = tab[lo];
-    const T *u = (const T *)d.u;
-    const T *v = (const T *)d.v;
+    const S *u = (const S *)d.u;
+    const S *v = (const S *)d.v;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = (int)(b - d.block_begin) * kSumRowsPerBlock;
     // Sums of u - u[0] and v - v[0]: with the shift close to the mean, the
     // one-pass variance sum(x^2)/n - mean^2 does not cancel catastrophically.
-    const T u0 = u[0], v0 = v[0];
+    const T u0 = load1(u), v0 = load1(v);
     T su = 0, suu = 0, sv = 0, svv = 0, sg = 0, se = 0;
     T mn = T(3.0e38), mx = T(-3.0e38);
     for (int i = r0 + w; i < min(r0 + kSumRowsPerBlock, d.nn); i += kSumBlock / 32) {
         const int ip = (i + 1 == d.nn) ? 0 : i + 1;
-        const T *ur = u + (int64_t)i * d.nm;
-        const T *un = u + (int64_t)ip * d.nm;
-        const T *vr = v + (int64_t)i * d.nm;
+        const S *ur = u + (int64_t)i * d.nm;
+        const S *un = u + (int64_t)ip * d.nm;
+        const S *vr = v + (int64_t)i * d.nm;
         for (int j = lane; j < d.nm; j += 32) {
             const int jp = (j + 1 == d.nm) ? 0 : j + 1;
-            const T x = ur[j];
-            const T g = fabs(un[j] - x) + fabs(ur[jp] - x);
-            const T xs = x - u0, ys = vr[j] - v0;
+            const T x = load1(ur + j);
+            const T g = fabs(load1(un + j) - x) + fabs(load1(ur + jp) - x);
+            const T xs = x - u0, ys = load1(vr + j) - v0;
             su += xs; suu += xs * xs; sv += ys; svv += ys * ys; sg += g;
             se += (g > threshold) ? T(1) : T(0);
             mn = min(mn, x); mx = max(mx, x);
@@ -130,13 +143,8 @@ k_summary_final(const SumDesc *__restrict__ tab, const Partial *__restrict__ par
     const double cnt = (double)d.nn * d.nm;
     const double mu = su / cnt, mv = sv / cnt;  // means of the shifted values
     double *o = out + (int64_t)blockIdx.x * kFields;
-    if (d.dtype64) {
-        o[0] = mu + ((const double *)d.u)[0];
-        o[4] = mv + ((const double *)d.v)[0];
-    } else {
-        o[0] = mu + (double)((const float *)d.u)[0];
-        o[4] = mv + (double)((const float *)d.v)[0];
-    }
+    o[0] = mu + first_value(d.u, d.dtype);
+    o[4] = mv + first_value(d.v, d.dtype);
     o[1] = fmax(0.0, suu / cnt - mu * mu);
     o[2] = mn;
     o[3] = mx;
@@ -170,7 +178,7 @@ int rdcnn_summary_workspace_bytes(const rdcnn_instance *inst, int n, size_t *byt
 int rdcnn_batch_summary(const rdcnn_instance *inst, int n, int dtype, double threshold, double *out,
                         void *workspace, size_t workspace_bytes, void *stream) {
     if (!inst || n < 1 || !out || !workspace) return set_error(RDCNN_EINVAL, "bad argument");
-    if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return set_error(RDCNN_EINVAL, "bad dtype");
+    if (dtype != RDCNN_F32 && dtype != RDCNN_F64 && !is_16bit(dtype)) return set_error(RDCNN_EINVAL, "bad dtype");
     size_t need = 0;
     const int rc = rdcnn_summary_workspace_bytes(inst, n, &need);
     if (rc < 0) return rc;
@@ -185,7 +193,7 @@ int rdcnn_batch_summary(const rdcnn_instance *inst, int n, int dtype, double thr
         tab[i].nn = (int)inst[i].nn; tab[i].nm = (int)inst[i].nm;
         tab[i].nblocks = (int)((inst[i].nn + kSumRowsPerBlock - 1) / kSumRowsPerBlock);
         tab[i].block_begin = blocks;
-        tab[i].dtype64 = dtype == RDCNN_F64 ? 1 : 0;
+        tab[i].dtype = dtype;
         blocks += tab[i].nblocks;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -195,12 +203,12 @@ int rdcnn_batch_summary(const rdcnn_instance *inst, int n, int dtype, double thr
     double *dout = (double *)((char *)part + align256((size_t)blocks * sizeof(Partial)));
     cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), n * sizeof(SumDesc), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_error(e, "copy summary table");
-    if (dtype == RDCNN_F64)
-        k_summary_partial<double><<<(unsigned)blocks, kSumBlock, 0, s>>>(dtab, n, threshold, part);
-    else
-        k_summary_partial<float><<<(unsigned)blocks, kSumBlock, 0, s>>>(dtab, n, (float)threshold, part);
+    e = with_dtype(dtype, [&](auto tag) {
+        using S = decltype(tag);
+        k_summary_partial<S><<<(unsigned)blocks, kSumBlock, 0, s>>>(dtab, n, (CT<S>)threshold, part);
+        return cudaGetLastError();
+    });
     count_launches(1);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "summary kernel");
     k_summary_final<<<n, 32, 0, s>>>(dtab, part, dout);
     count_launches(1);

@@ -140,7 +140,9 @@ def test_batch_model_validation(lib, L):
     assert run(L.F32, L.REACTION_CENN, L.BC_ZEROFLUX) == L.OK  # T = 0: validation only
     assert run(L.F32, L.REACTION_CENN, L.BC_PERIODIC) == L.OK
     assert run(L.F32, L.REACTION_FHN, L.BC_ZEROFLUX) == L.EINVAL  # Du < 0 is a diffusion error here
-    assert run(L.F64, L.REACTION_CENN, L.BC_PERIODIC) == L.EINVAL
+    for dt in (L.F64, L.BF16, L.F16):
+        assert run(dt, L.REACTION_CENN, L.BC_ZEROFLUX) == L.OK
+    assert run(7, L.REACTION_CENN, L.BC_PERIODIC) == L.EINVAL  # unknown dtype
     assert run(L.F32, L.REACTION_CENN, 2) == L.EINVAL
     assert run(L.F32, 3, L.BC_PERIODIC) == L.EINVAL
 
@@ -157,6 +159,10 @@ def test_batch_validation(lib, L):
     assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL  # NULL
     tab[1] = L.Instance(8, 8, p, 256, 520, 768, 1024)
     assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, None, 4096, n.value, None) == L.EINVAL  # misaligned
+    # 16-bit planes need 8-byte alignment only (T = 0: validation, no launch)
+    assert lib.rdcnn_batch_run(tab, 2, 0, L.BF16, 0, None, 4096, n.value, None) == L.OK
+    tab[1] = L.Instance(8, 8, p, 256, 516, 768, 1024)
+    assert lib.rdcnn_batch_run(tab, 2, 10, L.F16, 0, None, 4096, n.value, None) == L.EINVAL
     tab[1] = L.Instance(8, 8, p, 256, 512, 768, 1024)
     t = L.Tune(12, 0)
     assert lib.rdcnn_batch_run(tab, 2, 10, 0, 0, ctypes.byref(t), 4096, n.value, None) == L.EINVAL
@@ -271,7 +277,7 @@ def test_snapshot_summary_and_static_validation(lib, L):
     need = ctypes.c_size_t()
     assert lib.rdcnn_summary_workspace_bytes(tab, 0, ctypes.byref(need)) == L.EINVAL
     assert lib.rdcnn_summary_workspace_bytes(tab, 1, ctypes.byref(need)) == L.OK and need.value > 0
-    assert lib.rdcnn_batch_summary(tab, 1, L.BF16, 0.05, out, 4096, need.value, None) == L.EINVAL
+    assert lib.rdcnn_batch_summary(tab, 1, 7, 0.05, out, 4096, need.value, None) == L.EINVAL  # dtype
     assert lib.rdcnn_batch_summary(tab, 1, L.F32, 0.05, out, 4096, 8, None) == L.ESPACE
     tab[0] = L.Instance(8, 8, p, 0, 512, 0, 0)
     assert lib.rdcnn_batch_summary(tab, 1, L.F32, 0.05, out, 4096, need.value, None) == L.EINVAL

@@ -126,14 +126,77 @@ def test_batch_models_vs_oracle_and_single_grid(rd, oracle_mod, model, k):
             assert np.array_equal(v, v0)
 
 
-@pytest.mark.parametrize("model", [("fhn", "zeroflux"), ("cenn", "periodic")])
-def test_batch_f64_models_rejected(rd, model):
-    """The FP64 batched sweep is built for the torus FitzHugh-Nagumo and reaction-free models only."""
+@pytest.mark.parametrize("model", MODELS, ids=[f"{r}-{b}" for r, b in MODELS])
+def test_batch_f64_models_vs_oracle(rd, oracle_mod, model):
+    """The FP64 batched sweep with every model: the oracle within 1e-12 and the bits of
+    single-grid FP64 runs."""
     reaction, boundary = model
-    gene = CENN_GENE if reaction == "cenn" else inp.default_params()
-    b = rd.Batch([{"nn": 8, "nm": 8, "params": gene}], dtype=F64, reaction=reaction, boundary=boundary)
-    with pytest.raises(rd.RDCNNError):
-        b.run(3)
+    shapes = [(24, 40), (9, 6), (1, 2), (33, 130)]
+    specs = [{"nn": a, "nm": b, "params": dict(CENN_GENE, Du=0.05 + 0.01 * i) if reaction == "cenn"
+              else inp.default_params(Du=0.1 + 0.03 * i)} for i, (a, b) in enumerate(shapes)]
+    b = rd.Batch(specs, dtype=F64, reaction=reaction, boundary=boundary)
+    b.set_tune(k=3)
+    starts = []
+    for i, s in enumerate(specs):
+        x = inp.uniform_field(110 + i, s["nn"], s["nm"])
+        y = inp.uniform_field(210 + i, s["nn"], s["nm"])
+        starts.append((1.5 * x, 0.3 * y) if reaction == "cenn" else (x, y))
+        b.set_state(i, torch.from_numpy(starts[-1][0]), torch.from_numpy(starts[-1][1]))
+    T = 19
+    b.run(T)
+    torch.cuda.synchronize()
+    rx = {"fhn": oracle_mod.FHN, "none": oracle_mod.NONE, "cenn": oracle_mod.CENN}[reaction]
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    for i, s in enumerate(specs):
+        u0, v0 = starts[i]
+        u, v = (t.cpu().numpy() for t in b.state(i))
+        ref_u, ref_v = oracle_mod.run(u0, v0, s["params"], T, reaction=rx, boundary=bc)
+        assert normwise(u, ref_u) <= 1e-12 and normwise(v, ref_v) <= 1e-12, i
+        one = gpu_run(rd, u0, v0, s["params"], T, F64, "generic", reaction=reaction, boundary=boundary)
+        assert np.array_equal(u, one[0]) and np.array_equal(v, one[1]), i
+
+
+STORAGE = [("bf16", torch.bfloat16), ("f16", torch.float16)]
+MODELS16 = [("fhn", "periodic"), ("fhn", "zeroflux"), ("cenn", "zeroflux")]
+
+
+@pytest.mark.parametrize("k", [4, 8])
+@pytest.mark.parametrize("model", MODELS16, ids=[f"{r}-{b}" for r, b in MODELS16])
+@pytest.mark.parametrize("storage,dt", STORAGE, ids=[s for s, _ in STORAGE])
+def test_batch_16bit_vs_single_grid_and_storage_oracle(rd, oracle_mod, storage, dt, model, k):
+    """16-bit planes in the batched sweep: T = 4k runs as four launches of k steps, the same
+    rounding schedule as a single-grid temporal run at depth k (same bits) and as the
+    oracle's storage reference with blocks of k steps (bars of test_gpu_storage)."""
+    from test_gpu_storage import _close
+
+    reaction, boundary = model
+    shapes = [(37, 64), (5, 8), (128, 132)]
+    specs = [{"nn": a, "nm": b, "params": dict(CENN_GENE, Du=0.05 + 0.02 * i) if reaction == "cenn"
+              else inp.default_params(Du=0.1 + 0.05 * i)} for i, (a, b) in enumerate(shapes)]
+    b = rd.Batch(specs, dtype=dt, reaction=reaction, boundary=boundary)
+    b.set_tune(k=k)
+    starts = []
+    for i, s in enumerate(specs):
+        x = inp.uniform_field(120 + i, s["nn"], s["nm"])
+        y = inp.uniform_field(220 + i, s["nn"], s["nm"])
+        u0, v0 = (1.5 * x, 0.3 * y) if reaction == "cenn" else (x, y)
+        # start from the 16-bit values both sides use
+        u0 = torch.from_numpy(u0).to(dt).double().numpy()
+        v0 = torch.from_numpy(v0).to(dt).double().numpy()
+        starts.append((u0, v0))
+        b.set_state(i, torch.from_numpy(u0), torch.from_numpy(v0))
+    T = 4 * k
+    b.run(T)
+    torch.cuda.synchronize()
+    rx = {"fhn": oracle_mod.FHN, "none": oracle_mod.NONE, "cenn": oracle_mod.CENN}[reaction]
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    for i, s in enumerate(specs):
+        u0, v0 = starts[i]
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        one = gpu_run(rd, u0, v0, s["params"], T, dt, "temporal", k, reaction=reaction, boundary=boundary)
+        assert np.array_equal(u, one[0]) and np.array_equal(v, one[1]), i
+        su, sv = oracle_mod.run_storage(u0, v0, s["params"], T, k, storage, reaction=rx, boundary=bc)
+        _close(u, v, su.astype(np.float64), sv.astype(np.float64), storage, (i, s["nn"], s["nm"]))
 
 
 def test_sweep_zero_flux_cenn(rd):

@@ -37,6 +37,29 @@ def test_batch_summary_matches_definitions(rd, oracle_mod, dtype):
         assert got[i][7] == ref[7]  # the threshold test is taken in the state's precision on both sides
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16], ids=["bf16", "f16"])
+def test_batch_summary_16bit_planes(rd, oracle_mod, dtype):
+    """16-bit planes are read into FP32: the statistics equal the FP32 definitions on the
+    planes' values."""
+    specs = [{"nn": 64, "nm": 64, "params": inp.default_params(Du=0.3, Dv=1.0)},
+             {"nn": 37, "nm": 132, "params": inp.default_params(Du=0.5, Dv=0.8)}]
+    b = rd.Batch(specs, dtype=dtype)
+    for i, s in enumerate(specs):
+        x = inp.mid_patch(i, s["nn"], s["nm"], patch=16)
+        b.set_state(i, torch.from_numpy(x), torch.from_numpy(0.5 * x))
+    b.set_tune(k=4)
+    b.run(40)
+    thr = 0.02
+    got = b.summary(thr).numpy()
+    for i in range(len(specs)):
+        u, v = (t.float().cpu().numpy() for t in b.state(i))
+        ref = oracle_mod.summary(u, v, thr, precision=np.float32)
+        np.testing.assert_allclose(got[i][[0, 4, 6]], ref[[0, 4, 6]], rtol=1e-5, atol=1e-5)
+        np.testing.assert_allclose(got[i][[1, 5]], ref[[1, 5]], rtol=1e-4, atol=1e-7)
+        assert got[i][2] == ref[2] and got[i][3] == ref[3]
+        assert got[i][7] == ref[7]
+
+
 def test_grid_summary_full_size(rd, oracle_mod):
     N = 4096
     x = f32(inp.smooth_noise(0, N, N))
