@@ -205,3 +205,34 @@ def test_sweep_zero_flux_cenn(rd):
     genes = [dict(CENN_GENE, Du=d) for d in (0.05, 0.1)]
     out = search.sweep(genes, N=64, T=40, reaction="cenn", boundary="zeroflux", checkpoints=2)
     assert out["stats"].shape == (2, 3, 8) and np.isfinite(out["stats"]).all()
+
+
+def test_full_sweep_in_the_benchmark_launch_shape(rd, oracle_mod):
+    """All 256 instances of the seeded sweep (sides 128 .. 1024), k = 4 and 128-row strips as
+    the benchmark times them: after T = 500 two instances of each size match the oracle run
+    one by one (1e-5), and after T = 5000 sampled instances carry the bits of single-grid
+    runs of the same gene and start (FP32 results do not depend on the launch shape)."""
+    specs = inp.sweep_instances(0)
+    b = rd.Batch(specs, dtype=F32)
+    b.set_tune(k=4, rows=128)
+    xs = _load(b, specs, F32)
+    b.run(500)
+    torch.cuda.synchronize()
+    picked, seen = [], {}
+    for i, s in enumerate(specs):
+        if seen.get(s["nn"], 0) < 2:
+            seen[s["nn"]] = seen.get(s["nn"], 0) + 1
+            picked.append(i)
+    assert len(picked) == 8
+    for i in picked:
+        s = specs[i]
+        ref_u, ref_v = oracle_mod.run(xs[i], xs[i], s["params"], 500, nthreads=cpu_threads())
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        assert normwise(u, ref_u) <= 1e-5 and normwise(v, ref_v) <= 1e-5, (i, s["nn"])
+    b.run(4500)
+    torch.cuda.synchronize()
+    for i in (picked[0], picked[3], picked[5], picked[7], len(specs) - 1):
+        s = specs[i]
+        one = gpu_run(rd, xs[i], xs[i], s["params"], 5000, F32, "temporal", 8)
+        u, v = (t.double().cpu().numpy() for t in b.state(i))
+        assert np.array_equal(u, one[0]) and np.array_equal(v, one[1]), (i, s["nn"])

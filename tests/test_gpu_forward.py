@@ -147,11 +147,17 @@ def test_init_from_host_and_device(rd, oracle_mod):
 
 
 def test_smooth_noise_1024_T1000(rd, oracle_mod):
-    """Image-style workload: 1024^2 FP32, blurred-noise image, compared after 1000 steps."""
+    """Image-style workload: 1024^2 FP32, blurred-noise image, compared after 1000 steps, in
+    the AUTO shape and in the shapes the benchmark's autotuner picks for it (graph replay)."""
     x = f32(inp.smooth_noise(0, 1024, 1024))
     ref_u, ref_v = oracle_mod.run(x, x, inp.default_params(), 1000, nthreads=cpu_threads())
-    u, v = gpu_run(rd, x, x, inp.default_params(), 1000, F32, "auto")
-    assert normwise(u, ref_u) <= 1e-5 and normwise(v, ref_v) <= 1e-5
+    first = None
+    for variant, k, rows in (("auto", 0, 0), ("temporal", 3, 8), ("temporal", 4, 8), ("temporal", 4, 16)):
+        u, v = gpu_run(rd, x, x, inp.default_params(), 1000, F32, variant, k, rows=rows)
+        assert normwise(u, ref_u) <= 1e-5 and normwise(v, ref_v) <= 1e-5, (variant, k, rows)
+        if first is None:
+            first = (u, v)
+        assert np.array_equal(u, first[0]) and np.array_equal(v, first[1]), (variant, k, rows)
 
 
 @pytest.mark.parametrize("T,M", [(500, 1024), (1000, 2048)])
