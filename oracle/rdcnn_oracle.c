@@ -112,6 +112,20 @@ static double laplacian_bc(const double *f, int64_t nn, int64_t nm, int64_t i, i
     return (vert + horz) - 4.0 * f[i * nm + j];
 }
 
+/* Slope of the output function: 1 on (-1, 1), 0 outside; at the corners
+ * x = +-1, where the function has no derivative, the saturated side's 0. */
+static double cenn_slope(double x) {
+    return fabs(x) < 1.0 ? 1.0 : 0.0;
+}
+
+/* Sum of the four neighbour values of (i, j) (the stand-ins the boundary
+ * selects beyond an edge). */
+static double neighbour_sum(const double *f, int64_t nn, int64_t nm, int64_t i, int64_t j, int boundary) {
+    int64_t ip = neighbour_index(i + 1, nn, boundary), im = neighbour_index(i - 1, nn, boundary);
+    int64_t jp = neighbour_index(j + 1, nm, boundary), jm = neighbour_index(j - 1, nm, boundary);
+    return (f[im * nm + j] + f[ip * nm + j]) + (f[i * nm + jm] + f[i * nm + jp]);
+}
+
 /* Sum of the CeNN outputs y of the four neighbours of (i, j). */
 static double neighbour_output_sum(const double *x, int64_t nn, int64_t nm, int64_t i, int64_t j,
                                    int boundary) {
@@ -256,8 +270,20 @@ void oracle_scalar_map(double u0, double v0, const double *p, int64_t T,
  * grad[6] = dL/d{Du, Dv, a, b, eps, c}.
  * Forward states are rebuilt from checkpoints taken every S steps
  * (S = ceil(T / n_checkpoints), n_checkpoints <= 0 meaning ceil(sqrt(T))).
- * Returns 0, or -1 on bad sizes, a reaction other than FHN / NONE, a bad
- * boundary, or allocation failure.
+ * CeNN cell (reaction ORACLE_CENN; u = state x, v = offset w):
+ *   u+ = u + dt [ -u + c y(u) + Du sum_nbr y(u_n) + v ],  v+ = v,
+ * so with y' the slope of the output function (cenn_slope),
+ *   dL/du_k = lu_k + dt [ -lu_k + y'(u_k) (c lu_k + Du sum_{m: k nbr of m} lu_m) ]
+ *   dL/dv_k = lv_k + dt lu_k
+ * where the sum over the cells m that have k as a neighbour equals the
+ * neighbour sum of lu at k (adjacency is mutual, and under zero flux a
+ * missing neighbour stands for the cell itself on both sides).  Per step
+ *   dL/dDu += dt sum_k lu_k sum_nbr y(u_n)     dL/dc += dt sum_k lu_k y(u_k)
+ * and the other gene entries do not enter.  The output function has no
+ * derivative at +-1; the slope there is taken as 0.
+ *
+ * Returns 0, or -1 on bad sizes, an unknown reaction, a bad boundary, or
+ * allocation failure.
  *
  * Zero flux (oracle_adjoint_bc with ORACLE_ZEROFLUX): the forward map uses
  * the Laplacian whose missing neighbours are replaced by the cell itself.
@@ -272,7 +298,7 @@ int oracle_adjoint_bc(int64_t nn, int64_t nm, const double *u0, const double *v0
                       const double *lu_T, const double *lv_T, int64_t n_checkpoints,
                       double *lu0_out, double *lv0_out, double *grad, int nthreads) {
     if (nn <= 0 || nm <= 0 || T < 0) return -1;
-    if (reaction != ORACLE_FHN && reaction != ORACLE_NONE) return -1;
+    if (reaction != ORACLE_FHN && reaction != ORACLE_NONE && reaction != ORACLE_CENN) return -1;
     if (boundary != ORACLE_PERIODIC && boundary != ORACLE_ZEROFLUX) return -1;
     const size_t n = (size_t)nn * (size_t)nm;
     for (int g = 0; g < 6; ++g) grad[g] = 0.0;
@@ -311,7 +337,7 @@ int oracle_adjoint_bc(int64_t nn, int64_t nm, const double *u0, const double *v0
     memcpy(lv, lv_T, n * sizeof(double));
     const double dt = p[P_DT], Du = p[P_DU], Dv = p[P_DV];
     const double a = p[P_A], b = p[P_B], eps = p[P_EPS], c = p[P_C];
-    const int fhn = (reaction == ORACLE_FHN);
+    const int fhn = (reaction == ORACLE_FHN), cenn = (reaction == ORACLE_CENN);
 
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t t0 = s * S;
@@ -331,6 +357,11 @@ int oracle_adjoint_bc(int64_t nn, int64_t nm, const double *u0, const double *v0
                 for (int64_t j = 0; j < nm; ++j) {
                     const int64_t k = i * nm + j;
                     const double uk = u[k], vk = v[k], luk = lu[k], lvk = lv[k];
+                    if (cenn) {
+                        g[0] += luk * neighbour_output_sum(u, nn, nm, i, j, boundary);
+                        g[5] += luk * cenn_output(uk);
+                        continue;
+                    }
                     g[0] += luk * laplacian_bc(u, nn, nm, i, j, boundary);
                     g[1] += lvk * laplacian_bc(v, nn, nm, i, j, boundary);
                     if (fhn) {
@@ -348,6 +379,12 @@ int oracle_adjoint_bc(int64_t nn, int64_t nm, const double *u0, const double *v0
                 for (int64_t j = 0; j < nm; ++j) {
                     const int64_t k = i * nm + j;
                     const double uk = u[k], luk = lu[k], lvk = lv[k];
+                    if (cenn) {
+                        const double back = c * luk + Du * neighbour_sum(lu, nn, nm, i, j, boundary);
+                        lun[k] = luk + dt * (-luk + cenn_slope(uk) * back);
+                        lvn[k] = lvk + dt * luk;
+                        continue;
+                    }
                     double ru = 0.0, rv = 0.0;
                     if (fhn) {
                         ru = (c - uk * uk) * luk - eps * lvk;

@@ -35,6 +35,12 @@ MUTANTS = {
     "adj_dv_term": ("rv + Dv * laplacian_bc(lv", "rv + Du * laplacian_bc(lv"),
     "adj_zf_costate_on_torus": ("Du * laplacian_bc(lu, nn, nm, i, j, boundary)",
                                 "Du * laplacian_bc(lu, nn, nm, i, j, ORACLE_PERIODIC)"),
+    "adj_cenn_slope_ignored": ("lun[k] = luk + dt * (-luk + cenn_slope(uk) * back);",
+                               "lun[k] = luk + dt * (-luk + back);"),
+    "adj_cenn_no_leak": ("lun[k] = luk + dt * (-luk + cenn_slope(uk) * back);",
+                         "lun[k] = luk + dt * (cenn_slope(uk) * back);"),
+    "adj_cenn_offset_dropped": ("lvn[k] = lvk + dt * luk;", "lvn[k] = lvk;"),
+    "adj_cenn_grad_c_state": ("g[5] += luk * cenn_output(uk);", "g[5] += luk * uk;"),
     "adj_zf_grad_on_torus": ("g[1] += lvk * laplacian_bc(v, nn, nm, i, j, boundary);",
                              "g[1] += lvk * laplacian_bc(v, nn, nm, i, j, ORACLE_PERIODIC);"),
     "zf_ghost_past_edge": ("return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);", "return i < 0 ? 1 : (i > n - 1 ? n - 2 : i);"),

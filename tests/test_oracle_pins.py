@@ -271,24 +271,31 @@ def _loss(u, v, wu, wv):
     return float(np.sum(wu * u) + np.sum(wv * v))
 
 
-ADJ_CASES = [(inp.default_params(), "periodic", (7, 9)), (ODD_GENE, "periodic", (7, 9)),
-             (inp.default_params(), "zeroflux", (7, 9)), (ODD_GENE, "zeroflux", (2, 5))]
+CENN_ADJ_GENE = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.3, "Du": -0.2, "Dv": 0.0}
+ADJ_CASES = [(inp.default_params(), "fhn", "periodic", (7, 9)), (ODD_GENE, "fhn", "periodic", (7, 9)),
+             (inp.default_params(), "fhn", "zeroflux", (7, 9)), (ODD_GENE, "fhn", "zeroflux", (2, 5)),
+             (CENN_ADJ_GENE, "cenn", "periodic", (7, 9)), (CENN_ADJ_GENE, "cenn", "zeroflux", (6, 5))]
 
 
-@pytest.mark.parametrize("gene,boundary,shape", ADJ_CASES,
-                         ids=["default-torus", "odd-torus", "default-zeroflux", "odd-zeroflux-2x5"])
-def test_adjoint_matches_central_differences(oracle_mod, gene, boundary, shape):
+@pytest.mark.parametrize("gene,reaction,boundary,shape", ADJ_CASES,
+                         ids=["default-torus", "odd-torus", "default-zeroflux", "odd-zeroflux-2x5",
+                              "cenn-torus", "cenn-zeroflux-6x5"])
+def test_adjoint_matches_central_differences(oracle_mod, gene, reaction, boundary, shape):
     """Linear loss L = <wu, u_T> + <wv, v_T>; FD of the forward map in every gene entry and
-    along random directions of the start state (the forward map is pinned on its own)."""
+    along random directions of the start state (the forward map is pinned on its own).  The
+    CeNN start state spans both saturated arms (no cell sits within the FD step of a corner
+    of the output function along these seeded trajectories)."""
     nn, nm = shape
     T = 25
     bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
-    x = inp.uniform_field(21, nn, nm)
+    rx = oracle_mod.CENN if reaction == "cenn" else oracle_mod.FHN
+    scale = 1.7 if reaction == "cenn" else 1.0
+    x = scale * inp.uniform_field(21, nn, nm)
     y = inp.uniform_field(22, nn, nm)
     wu = inp.uniform_field(23, nn, nm)
     wv = inp.uniform_field(24, nn, nm)
-    run = lambda a, b, g: oracle_mod.run(a, b, g, T, boundary=bc)
-    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=4, boundary=bc)
+    run = lambda a, b, g: oracle_mod.run(a, b, g, T, reaction=rx, boundary=bc)
+    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=4, reaction=rx, boundary=bc)
     names = ["Du", "Dv", "a", "b", "eps", "c"]
     for k, name in enumerate(names):
         h = 1e-5 * max(1.0, abs(gene[name]))
@@ -330,6 +337,25 @@ def test_adjoint_of_pure_diffusion_is_diffusion(oracle_mod, boundary):
     fu, fv = oracle_mod.run(wu, wv, gene, 13, reaction=oracle_mod.NONE, boundary=bc)
     assert np.array_equal(lu0, fu) and np.array_equal(lv0, fv)
     assert np.all(g[2:] == 0.0)
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "zeroflux"])
+def test_cenn_adjoint_without_feedback_is_a_closed_form(oracle_mod, boundary):
+    """CeNN cell with c = Du = 0: u+ = (1 - dt) u + dt v, v+ = v, a linear map whose transpose
+    gives lu_0 = (1 - dt)^T lu_T and lv_0 = lv_T + (1 - (1 - dt)^T) lu_T; only the c and Du
+    entries of the gene gradient can be non-zero."""
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    gene = {"dt": 0.07, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 0.0, "Du": 0.0, "Dv": 0.0}
+    T = 19
+    x = 1.5 * inp.uniform_field(44, 5, 6)
+    y = inp.uniform_field(45, 5, 6)
+    wu = inp.uniform_field(46, 5, 6)
+    wv = inp.uniform_field(47, 5, 6)
+    lu0, lv0, g = oracle_mod.adjoint(x, y, gene, T, wu, wv, reaction=oracle_mod.CENN, boundary=bc)
+    q = (1.0 - gene["dt"]) ** T
+    np.testing.assert_allclose(lu0, q * wu, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(lv0, wv + (1.0 - q) * wu, rtol=1e-13, atol=1e-15)
+    assert np.all(g[1:5] == 0.0)
 
 
 def test_adjoint_zero_steps(oracle_mod):
