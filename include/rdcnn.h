@@ -122,8 +122,7 @@ typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
  * gets no RDCNN_WARN_CFL check).  Pure host call (no CUDA work).
  * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL.
  * A ZEROFLUX or CENN handle supports rdcnn_run / rdcnn_run_snapshots with
- * every variant but RDCNN_VARIANT_TEMPORAL2; rdcnn_adjoint takes ZEROFLUX
- * FHN / NONE handles and rejects CENN ones (RDCNN_EINVAL). */
+ * every variant but RDCNN_VARIANT_TEMPORAL2, and rdcnn_adjoint. */
 int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p,
                  int boundary, int dtype, int reaction);
 
@@ -301,8 +300,10 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
  * states (0 = ceil(sqrt(T))).  All planes are device planes of the handle's
  * size and dtype; the bound u/v/workspace of the handle are not touched.
  * The handle's boundary applies (the zero-flux Laplacian, like the periodic
- * one, is symmetric, so the co-state diffuses under the same operator);
- * reaction FHN or NONE (CENN: RDCNN_EINVAL).
+ * one, is symmetric, so the co-state diffuses under the same operator), and
+ * its reaction: for CENN handles grad holds dL/dDu (the neighbour feedback
+ * weight) and dL/dc (the self-feedback weight), the other entries are 0, and
+ * the output function's slope is taken as 1 on (-1, 1) and 0 elsewhere.
  * Synchronises the handle's stream (grad is a host result). */
 int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
                   const void *dLdu_T, const void *dLdv_T, int64_t n_checkpoints,

@@ -19,6 +19,15 @@
 // the reflected image of the real one, forward and backward), so the
 // pipeline's mirrored halos serve both.
 //
+// The Chua-Yang cell (u+ = u + dt [-u + c y(u) + Du sum_nbr y(u_n) + v],
+// v+ = v) has
+//   dL/du = lu + dt [ -lu + y'(u) (c lu + Du sum_nbr lu) ],  dL/dv = lv + dt lu
+// with y' = 1 on (-1, 1) and 0 elsewhere (the corners included), and per step
+//   dL/dDu += dt sum lu sum_nbr y(u_n) = dt sum y(u) sum_nbr lu
+//   dL/dc  += dt sum lu y(u)
+// (again by the symmetry of the neighbour relation), so it too reads the
+// state at the centre cell only.
+//
 // Driver: a forward sweep stores n_ck checkpoints (every S = ceil(T/n_ck)
 // steps).  Segments are then processed last to first: k_forward_all rebuilds
 // the segment's states K per launch (every stage of the temporal pipeline is
@@ -52,6 +61,13 @@ template <typename T>
 AdjCoef<T> make_adj_coef(const rdcnn_params &p, int reaction) {
     const bool fhn = (reaction == RDCNN_REACTION_FHN);
     AdjCoef<T> q;
+    if (reaction == RDCNN_REACTION_CENN) {  // cm4 = c: the self-feedback weight
+        q.dt = T(p.dt); q.Du = T(p.Du); q.Dv = T(0);
+        q.cm4 = T(p.c);
+        q.meps = q.ebm4 = q.mb = T(0);
+        q.a = 0.0; q.eps = 0.0;
+        return q;
+    }
     q.dt = T(p.dt); q.Du = T(p.Du); q.Dv = T(p.Dv);
     q.cm4 = T((fhn ? p.c : 0.0) - 4.0 * p.Du);
     q.meps = T(fhn ? -p.eps : 0.0);
@@ -135,6 +151,19 @@ struct ReversePolicy {
             // co-state update with the centre term folded in, like the forward:
             //   lu + dt [ Du s(lu) + (c - 4 Du - u^2) lu - eps lv ]
             //   lv + dt [ Dv s(lv) + (eps b - 4 Dv) lv - lu ]
+            if constexpr (RX == RX_CENN) {
+                // -lu + y'(u) (c lu + Du sum_nbr lu); y' in {0, 1}, so the product is exact
+                const T slope = fabs(uc) < T(1) ? T(1) : T(0);
+                const T back = fma_rn(p.Du, su, mul_rn(p.cm4, luc));
+                out.u[e] = fma_rn(p.dt, fma_rn(slope, back, -luc), luc);
+                out.v[e] = fma_rn(p.dt, luc, lvc);
+                if (own) {
+                    const T yc = clamp1(uc);
+                    rg[0] = fma_rn(yc, su, rg[0]);   // y(u) sum_nbr lu  (Du)
+                    rg[5] = fma_rn(luc, yc, rg[5]);  // lu y(u)          (c)
+                }
+                continue;
+            }
             T ru, rv;
             if (RX == RX_FHN) {
                 ru = fma_rn(fma_rn(-uc, uc, p.cm4), luc, mul_rn(p.meps, lvc));
@@ -170,6 +199,10 @@ struct ReversePolicy {
         for (int q = 0; q < 6; ++q) rg[q] = warp_sum_t(rg[q]);
         if ((threadIdx.x & 31) == 0) {
             slot[0] += (double)rg[0];
+            if (RX == RX_CENN) {
+                slot[5] += (double)rg[5];
+                return;
+            }
             slot[1] += (double)rg[1];
             if (RX == RX_FHN) {
                 slot[2] -= p.eps * (double)rg[2];
@@ -276,17 +309,6 @@ cudaError_t pipe_smem_optin() {
     return done;
 }
 
-// Dispatch of the adjoint's models: FitzHugh-Nagumo or no reaction, torus or
-// zero flux, as compile-time tags f(IntC<RX>{}, IntC<BC>{}).
-template <class F>
-cudaError_t with_adj_model(int reaction, int boundary, F &&f) {
-    const bool zf = (boundary == RDCNN_BC_ZEROFLUX);
-    if (reaction == RDCNN_REACTION_FHN)
-        return zf ? f(IntC<RX_FHN>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_FHN>{}, IntC<BC_WRAP>{});
-    if (reaction == RDCNN_REACTION_NONE)
-        return zf ? f(IntC<RX_NONE>{}, IntC<BC_MIRROR>{}) : f(IntC<RX_NONE>{}, IntC<BC_WRAP>{});
-    return cudaErrorInvalidValue;
-}
 
 template <typename T, int K>
 cudaError_t reverse_launch_k(int reaction, int boundary, const void *lu, const void *lv, void *lun, void *lvn,
@@ -295,7 +317,7 @@ cudaError_t reverse_launch_k(int reaction, int boundary, const void *lu, const v
     const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const AdjCoef<T> c = make_adj_coef<T>(p, reaction);
     const size_t smem = pipe_smem_bytes<T, K>();
-    return with_adj_model(reaction, boundary, [&](auto rx, auto bc) {
+    return with_model(reaction, boundary, [&](auto rx, auto bc) {
         constexpr int RX = decltype(rx)::value;
         constexpr int BC = decltype(bc)::value;
         const cudaError_t oe = pipe_smem_optin<T, K, RX, BC>();
@@ -314,7 +336,7 @@ cudaError_t forward_all_launch_k(int reaction, int boundary, const void *u, cons
                                  const rdcnn_params &p, cudaStream_t s) {
     const unsigned grid = (unsigned)((sh.nwarps + kTemporalWarps - 1) / kTemporalWarps);
     const Coef<T> c = make_coef<T>(p, reaction);
-    return with_adj_model(reaction, boundary, [&](auto rx, auto bc) {
+    return with_model(reaction, boundary, [&](auto rx, auto bc) {
         const cudaError_t e = launch_k(k_forward_all<T, K, 1, decltype(rx)::value, decltype(bc)::value>, grid,
                                        kPipeBlock, 0, s, (const T *)u, (const T *)v, pl, (int)nn, (int)nm,
                                        sh.bands, sh.nwarps, sh.rows, c);
@@ -476,8 +498,6 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
-    if (reaction == RDCNN_REACTION_CENN)
-        return set_error(RDCNN_EINVAL, "the adjoint supports the FHN / NONE models only");
     if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)

@@ -404,16 +404,19 @@ class RDCNNFunction(torch.autograd.Function):
 
     Forward runs T steps of Eq. 1; backward runs the reverse-time adjoint
     (``rdcnn_adjoint``, sqrt(T) checkpoints) and returns dL/du0, dL/dv0, dL/dtheta.
-    ``boundary``: "periodic" (the paper's torus) or "zeroflux".
+    ``boundary``: "periodic" (the paper's torus) or "zeroflux"; ``reaction``: "fhn", "none" or
+    "cenn" (then u0 is the cell state, v0 the offset plane, and theta's Du / c entries the
+    neighbour / self feedback weights).
     """
 
     @staticmethod
     def forward(ctx, u0, v0, theta, T: int, dt: float = 0.1, n_checkpoints: int = 0,
-                boundary: str = "periodic"):
+                boundary: str = "periodic", reaction: str = "fhn"):
         th = [float(x) for x in theta.detach().cpu().tolist()]
         params = dict(zip(GRAD_NAMES, th))
         params["dt"] = float(dt)
-        g = Grid(u0.shape[0], u0.shape[1], params, dtype=u0.dtype, device=u0.device, boundary=boundary)
+        g = Grid(u0.shape[0], u0.shape[1], params, dtype=u0.dtype, device=u0.device, boundary=boundary,
+                 reaction=reaction)
         g.set_state(u0.detach(), v0.detach())
         g.run(int(T))
         uT, vT = g.state()
@@ -435,4 +438,4 @@ class RDCNNFunction(torch.autograd.Function):
             gv = torch.zeros_like(v0)
         du0, dv0, gp = g.adjoint(ctx.T, u0, v0, gu.contiguous(), gv.contiguous(), ctx.nck)
         gtheta = torch.tensor([gp[k] for k in GRAD_NAMES], dtype=ctx.theta_dtype, device=ctx.theta_device)
-        return du0, dv0, gtheta, None, None, None, None
+        return du0, dv0, gtheta, None, None, None, None, None

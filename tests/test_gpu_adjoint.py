@@ -235,9 +235,63 @@ def test_zeroflux_autograd_gradcheck_f64(rd):
     assert gradcheck(f, (u0, v0, theta), eps=1e-6, atol=1e-7, rtol=1e-5)
 
 
-def test_cenn_adjoint_rejected(rd):
-    gene = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.2, "Du": 0.1, "Dv": 0.0}
-    g = rd.Grid(8, 8, gene, dtype=F32, reaction="cenn")
-    z = torch.zeros((8, 8), dtype=F32, device="cuda")
-    with pytest.raises(rd.RDCNNError):
-        g.adjoint(3, z, z, z, z)
+CENN_ADJ = {"dt": 0.1, "a": 0.0, "b": 0.0, "eps": 0.0, "c": 1.3, "Du": -0.2, "Dv": 0.0}
+CENN_SHAPES = [(24, 40), (9, 6), (33, 130)]
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "zeroflux"])
+@pytest.mark.parametrize("shape", CENN_SHAPES, ids=[f"{a}x{b}" for a, b in CENN_SHAPES])
+def test_f64_cenn_adjoint_matches_oracle(rd, oracle_mod, shape, boundary):
+    """Chua-Yang cell: the reverse step gates the fed-back co-state by the output function's
+    slope; the oracle adjoint is pinned to central differences of the CeNN forward map."""
+    nn, nm = shape
+    T = 31
+    x = 1.7 * inp.uniform_field(81, nn, nm)
+    y = inp.uniform_field(82, nn, nm)
+    wu = inp.uniform_field(83, nn, nm)
+    wv = inp.uniform_field(84, nn, nm)
+    g = rd.Grid(nn, nm, CENN_ADJ, dtype=F64, reaction="cenn", boundary=boundary)
+    du, dv, gp = g.adjoint(T, _dev(x, F64), _dev(y, F64), _dev(wu, F64), _dev(wv, F64), 5)
+    torch.cuda.synchronize()
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    ou, ov, og = oracle_mod.adjoint(x, y, CENN_ADJ, T, wu, wv, n_checkpoints=5, reaction=oracle_mod.CENN,
+                                    boundary=bc)
+    assert normwise(du.cpu().numpy(), ou) < 1e-10 and normwise(dv.cpu().numpy(), ov) < 1e-10
+    got = np.array([gp[k] for k in NAMES])
+    np.testing.assert_allclose(got, og, rtol=1e-9, atol=1e-12)
+    assert np.all(got[1:5] == 0.0)
+
+
+def test_f32_cenn_adjoint_short_horizon(rd, oracle_mod):
+    N, T = 256, 20
+    x = f32(1.7 * inp.uniform_field(85, N, N))
+    y = f32(inp.uniform_field(86, N, N))
+    gu = f32(inp.uniform_field(87, N, N)) / (N * N)
+    gv = f32(inp.uniform_field(88, N, N)) / (N * N)
+    g = rd.Grid(N, N, CENN_ADJ, dtype=F32, reaction="cenn")
+    du, dv, gp = g.adjoint(T, _dev(x, F32), _dev(y, F32), _dev(gu, F32), _dev(gv, F32))
+    torch.cuda.synchronize()
+    ou, ov, og = oracle_mod.adjoint(x, y, CENN_ADJ, T, gu, gv, reaction=oracle_mod.CENN)
+    assert normwise(du.double().cpu().numpy(), ou) <= 1e-5 and normwise(dv.double().cpu().numpy(), ov) <= 1e-5
+    got = np.array([gp[k] for k in NAMES])
+    np.testing.assert_allclose(got, og, rtol=1e-5, atol=1e-6 * np.linalg.norm(og))
+
+
+def test_cenn_autograd_fit_step(rd):
+    """Template learning through RDCNNFunction: one gradient step on the CeNN feedback
+    weights (Du, c) lowers the distance to a target state produced by other weights."""
+    N, T = 48, 30
+    x = _dev(f32(1.5 * inp.uniform_field(89, N, N)), F32)
+    w = _dev(f32(0.2 * inp.uniform_field(90, N, N)), F32)
+    true = dict(CENN_ADJ, c=1.1, Du=0.15)
+    target, _ = rd.RDCNNFunction.apply(x, w, torch.tensor([true[k] for k in NAMES], dtype=F64, device="cuda"),
+                                       T, 0.1, 0, "periodic", "cenn")
+    theta = torch.tensor([CENN_ADJ[k] for k in NAMES], dtype=F64, device="cuda", requires_grad=True)
+    uT, _ = rd.RDCNNFunction.apply(x, w, theta, T, 0.1, 0, "periodic", "cenn")
+    loss = torch.mean((uT - target.detach()) ** 2)
+    loss.backward()
+    assert torch.isfinite(theta.grad).all() and theta.grad[1:5].abs().max().item() == 0.0
+    with torch.no_grad():
+        th2 = theta - 1e-2 * theta.grad / theta.grad.norm()
+    u2, _ = rd.RDCNNFunction.apply(x, w, th2, T, 0.1, 0, "periodic", "cenn")
+    assert torch.mean((u2 - target) ** 2).item() < loss.item()
