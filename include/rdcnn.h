@@ -34,8 +34,9 @@
  * and rounds the result to nearest (ties to even) when it stores it.  This
  * halves the bytes per cell-step of the single-step kernel (8 B instead of
  * 16) at the cost of one 16-bit rounding per launch.  Supported by
- * rdcnn_init / set_state / run / get_state / run_snapshots / plan; the
- * batched, adjoint, static-scratch and TEMPORAL2 paths return RDCNN_EINVAL.
+ * rdcnn_init / set_state / run / get_state / run_snapshots / plan and by
+ * the batched sweep (rdcnn_batch_run*, rdcnn_batch_summary); the adjoint,
+ * static-scratch and TEMPORAL2 paths return RDCNN_EINVAL.
  *
  * Conventions shared by every entry point
  *  - Layout: one plane per field, row-major [NN][NM], element (i, j) at
@@ -121,8 +122,7 @@ typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
  * for CENN, whose feedback weights c and Du may have either sign (and which
  * gets no RDCNN_WARN_CFL check).  Pure host call (no CUDA work).
  * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL.
- * A ZEROFLUX or CENN handle supports rdcnn_run / rdcnn_run_snapshots with
- * every variant but RDCNN_VARIANT_TEMPORAL2, and rdcnn_adjoint. */
+ * A ZEROFLUX or CENN handle supports every entry point and variant. */
 int rdcnn_create(rdcnn_t **out, int64_t nn, int64_t nm, const rdcnn_params *p,
                  int boundary, int dtype, int reaction);
 
@@ -177,9 +177,9 @@ int rdcnn_set_state(rdcnn_t *h, const void *u0, const void *v0, int on_device);
  * variants need NM to be a multiple of 4 (F32, BF16, F16) or 2 (F64) and
  * 16-byte (8-byte for BF16 / F16) aligned buffers;
  * AUTO falls back to GENERIC otherwise, an explicit request returns
- * RDCNN_EINVAL.  The handle's reaction and boundary apply to every variant
- * except RDCNN_VARIANT_TEMPORAL2, which returns RDCNN_EINVAL for ZEROFLUX
- * or CENN handles.  Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
+ * RDCNN_EINVAL.  The handle's reaction and boundary apply to every
+ * variant; RDCNN_VARIANT_TEMPORAL2 takes FP32 / FP64 handles only.
+ * Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ECUDA. */
 int rdcnn_run(rdcnn_t *h, int64_t T, int variant, int k);
 
 /* RDCNN_VARIANT_TEMPORAL_WIDE: the temporal pipeline with 8 values per lane

@@ -45,9 +45,8 @@ def tune_grid(grid, x=None, trial_steps: int = 48, force: bool = False) -> dict:
         _cache[key] = best
         return dict(best)
     cands = GRID_CANDIDATES_F64 if grid.dtype == torch.float64 else GRID_CANDIDATES_F32
-    if getattr(grid, "boundary", "periodic") != "periodic" or grid.reaction == "cenn" \
-            or grid.dtype in (torch.bfloat16, torch.float16):
-        cands = [c for c in cands if c[0] != "temporal2"]  # periodic FHN / NONE in FP32 / FP64 only
+    if grid.dtype in (torch.bfloat16, torch.float16):
+        cands = [c for c in cands if c[0] != "temporal2"]  # FP32 / FP64 planes only
     if grid.nm % 8 != 0:
         cands = [c for c in cands if c[0] != "temporal_wide"]  # 8 values per lane
     T = 240 * max(1, trial_steps // 48)  # divisible by every candidate depth

@@ -204,10 +204,8 @@ static int resolve_variant(const rdcnn_t *h, bool vec_ok, bool wide_ok, int *var
         return set_error(RDCNN_EINVAL,
                          "vectorised variants need NM %% %d == 0 and %d-byte aligned buffers",
                          vec_width(h->dtype), (int)vec_align(h->dtype));
-    if (*variant == RDCNN_VARIANT_TEMPORAL2 &&
-        (h->boundary != RDCNN_BC_PERIODIC || h->reaction == RDCNN_REACTION_CENN || is_16bit(h->dtype)))
-        return set_error(RDCNN_EINVAL,
-                         "RDCNN_VARIANT_TEMPORAL2 supports the periodic FHN / NONE models in FP32 / FP64 only");
+    if (*variant == RDCNN_VARIANT_TEMPORAL2 && is_16bit(h->dtype))
+        return set_error(RDCNN_EINVAL, "RDCNN_VARIANT_TEMPORAL2 supports FP32 / FP64 planes only");
     if (*variant == RDCNN_VARIANT_TEMPORAL || *variant == RDCNN_VARIANT_TEMPORAL2) {
         if (*k == 0) *k = h->tune_k ? h->tune_k : default_k(h->dtype, h->nn, h->nm);
         if (*k < 1 || *k > max_k(h->dtype))
@@ -238,7 +236,7 @@ static cudaError_t launch_one(const rdcnn_t *h, int variant, int kk, const void 
         return launch_temporal_wide(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
                                     h->tune_rows, s);  // 0 = chosen by the launcher
     if (variant == RDCNN_VARIANT_TEMPORAL2 && kk >= 2)
-        return launch_temporal_split(h->dtype, h->reaction, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
+        return launch_temporal_split(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,
                                      h->tune_rows, s);
     if (variant == RDCNN_VARIANT_TEMPORAL || variant == RDCNN_VARIANT_TEMPORAL2)
         return launch_temporal(h->dtype, h->reaction, h->boundary, kk, cu, cv, nu, nv, h->nn, h->nm, h->p,

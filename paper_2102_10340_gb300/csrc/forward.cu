@@ -26,13 +26,20 @@
 // and generic kernels clamp neighbour indices into the grid (the ghost cell
 // is the edge cell); the temporal kernel loads mirrored halos instead
 // (temporal.cuh).  k_temporal's launchers live in temporal_launch.cuh and are
-// instantiated in the temporal_*.cu units, which compile in parallel.
+// instantiated in the temporal_*.cu units, the warp-pair variant's
+// (k_temporal_split) in split_launch.cuh and the split_*.cu units; they
+// compile in parallel.
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
 #include "temporal.cuh"
-#include "temporal_split.cuh"
+#include "split_launch.cuh"
+
+// the warp-pair kernels compile in split_f32a.cu .. split_f32c.cu and split_f64.cu
+RDK_EXTERN_SPLIT(float, 2) RDK_EXTERN_SPLIT(float, 3) RDK_EXTERN_SPLIT(float, 4) RDK_EXTERN_SPLIT(float, 5)
+RDK_EXTERN_SPLIT(float, 6) RDK_EXTERN_SPLIT(float, 7) RDK_EXTERN_SPLIT(float, 8)
+RDK_EXTERN_SPLIT(double, 2) RDK_EXTERN_SPLIT(double, 3) RDK_EXTERN_SPLIT(double, 4)
 
 namespace rdk {
 
@@ -120,19 +127,6 @@ k_step1(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
 }
 
 // --------------------------------------------------------------------------- temporal blocking
-
-// One warp pair per (band, strip): stages split between the two warps
-// (temporal_split.cuh).  Both warps of a pair see the same `item`.
-template <typename T, int K, int RX>
-__global__ void __launch_bounds__(kSplitBlock)
-k_temporal_split(const T *__restrict__ u, const T *__restrict__ v, T *__restrict__ un,
-                 T *__restrict__ vn, int nn, int nm, int bands, int nitems, int rows, Coef<T> p) {
-    pdl_wait();
-    const int item = blockIdx.x * kSplitPairs + ((threadIdx.x >> 5) >> 1);
-    if (item >= nitems) return;  // the whole pair, before any barrier
-    temporal_split_item<T, K, RX>(item, bands, u, v, un, vn, nn, nm, rows, p);
-    pdl_trigger();
-}
 
 // --------------------------------------------------------------------------- generic
 
@@ -235,51 +229,6 @@ int auto_rows_temporal(int K, int64_t nn, int64_t nm, int bands, int blocks_per_
 
 namespace {
 
-template <typename T, int K, int RX>
-int split_blocks_per_sm() {
-    static int cached = -1;
-    if (cached < 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_temporal_split<T, K, RX>, kSplitBlock, 0) !=
-            cudaSuccess)
-            nb = 1;
-        cached = nb;
-    }
-    return cached;
-}
-
-template <typename T, int K>
-int split_rows(int reaction, int64_t nn, int64_t nm, int rows) {
-    if (rows > 0) return rows;
-    constexpr int V = Vec<T>::N;
-    constexpr int H = (K + V - 1) / V;
-    constexpr int OUTW = (32 - 2 * H) * V;
-    const int bands = (int)((nm + OUTW - 1) / OUTW);
-    const int bps = reaction == RDCNN_REACTION_FHN ? split_blocks_per_sm<T, K, RX_FHN>()
-                                                   : split_blocks_per_sm<T, K, RX_NONE>();
-    return auto_rows_temporal(K, nn, nm, bands, bps, kSplitPairs);
-}
-
-template <typename T, int K>
-cudaError_t split_tk(int reaction, const void *u, const void *v, void *un, void *vn, int64_t nn,
-                     int64_t nm, const rdcnn_params &p, int rows, cudaStream_t s) {
-    constexpr int V = Vec<T>::N;
-    constexpr int H = (K + V - 1) / V;
-    constexpr int OUTW = (32 - 2 * H) * V;
-    const int bands = (int)((nm + OUTW - 1) / OUTW);
-    rows = split_rows<T, K>(reaction, nn, nm, rows);
-    const int strips = (int)((nn + rows - 1) / rows);
-    const int64_t nitems = (int64_t)bands * strips;
-    const unsigned grid = (unsigned)((nitems + kSplitPairs - 1) / kSplitPairs);
-    const Coef<T> c = make_coef<T>(p, reaction);
-    const cudaError_t e = launch_k(reaction == RDCNN_REACTION_FHN ? k_temporal_split<T, K, RX_FHN>
-                                                                 : k_temporal_split<T, K, RX_NONE>,
-                                   grid, kSplitBlock, 0, s, (const T *)u, (const T *)v, (T *)un, (T *)vn,
-                                   (int)nn, (int)nm, bands, (int)nitems, rows, c);
-    count_launches(1);
-    return e;
-}
-
 template <typename T>
 cudaError_t generic_t(int reaction, int boundary, const void *u, const void *v, void *un, void *vn,
                       int64_t nn, int64_t nm, const rdcnn_params &p, cudaStream_t s) {
@@ -344,11 +293,10 @@ cudaError_t launch_temporal_wide(int dtype, int reaction, int boundary, int k, c
     });
 }
 
-// FP32 / FP64 storage, periodic FitzHugh-Nagumo / pure diffusion only (the caller checks).
-cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
+// FP32 / FP64 storage (the caller checks), every model.
+cudaError_t launch_temporal_split(int dtype, int reaction, int boundary, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                                   int rows, cudaStream_t s) {
-    if (reaction != RDCNN_REACTION_FHN && reaction != RDCNN_REACTION_NONE) return cudaErrorInvalidValue;
     if (dtype != RDCNN_F32 && dtype != RDCNN_F64) return cudaErrorInvalidValue;
     return with_dtype(dtype, [&](auto tag) {
         using T = decltype(tag);
@@ -356,7 +304,7 @@ cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u,
             constexpr int K = decltype(kk)::value;
             if constexpr (K >= 2 && K <= MaxDepth<T>::value &&
                           is_f32_f64<T>())
-                return split_tk<T, K>(reaction, u, v, un, vn, nn, nm, p, rows, s);
+                return split_tk<T, K>(reaction, boundary, u, v, un, vn, nn, nm, p, rows, s);
             else
                 return cudaErrorInvalidValue;
         });
@@ -395,7 +343,7 @@ int plan_rows(int dtype, int reaction, int boundary, int variant, int k, int64_t
             if constexpr (K <= MaxDepth<T>::value) {
                 if constexpr (K >= 2 && is_f32_f64<T>()) {
                     if (variant == RDCNN_VARIANT_TEMPORAL2) {
-                        out = split_rows<T, K>(reaction, nn, nm, rows);
+                        out = split_rows<T, K>(reaction, boundary, nn, nm, rows);
                         return cudaSuccess;
                     }
                 }

@@ -126,9 +126,9 @@ cudaError_t launch_temporal(int dtype, int reaction, int boundary, int k, const 
 cudaError_t launch_temporal_wide(int dtype, int reaction, int boundary, int k, const void *u,
                                  const void *v, void *un, void *vn, int64_t nn, int64_t nm,
                                  const rdcnn_params &p, int rows, cudaStream_t s);
-// The temporal pipeline with the K stages split across a warp pair (k >= 2);
-// periodic boundary, FitzHugh-Nagumo or no reaction.
-cudaError_t launch_temporal_split(int dtype, int reaction, int k, const void *u, const void *v,
+// The temporal pipeline with the K stages split across a warp pair (k >= 2;
+// FP32 / FP64 planes, every model).
+cudaError_t launch_temporal_split(int dtype, int reaction, int boundary, int k, const void *u, const void *v,
                                   void *un, void *vn, int64_t nn, int64_t nm, const rdcnn_params &p,
                                   int rows, cudaStream_t s);
 cudaError_t launch_generic(int dtype, int reaction, int boundary, const void *u, const void *v,

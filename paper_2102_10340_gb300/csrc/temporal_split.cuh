@@ -13,7 +13,9 @@
 // total + 1 beats, so their barrier counts always match; the only early exit
 // (a pair without work) happens before any barrier and for both warps.
 //
-// Same arithmetic and the same cells as temporal_strip: identical bits.
+// Same arithmetic and the same cells as temporal_strip: identical bits, on
+// the torus and under zero flux (the producer walks the reflected rows and
+// reverses mirrored lane vectors exactly as temporal_strip does).
 //
 // Light-cone fill (as in temporal.cuh): global stage s first matters at the
 // equivalent single-warp beat 2s + 2.  The producer's beat m is that beat;
@@ -47,10 +49,10 @@ __device__ __forceinline__ void hand_read(const Handoff<T> &h, int k, Slice<T> &
 
 // Producer beat: input row m from the ring through stages 1 .. K1; the stage-K1
 // row (input-row index m - K1) goes to handoff slot m % 2.
-template <typename T, int K1, int RX, int PH, int ACT = K1>
+template <typename T, int K1, int RX, int BC, int PH, int ACT = K1>
 __device__ __forceinline__ void split_producer_beat(int m, int total, Slice<T> (&W)[3][K1],
                                                     const RowRing<T> &ring, const Handoff<T> &hand,
-                                                    int &g_issue, int nn, int nm, int lc,
+                                                    RowWalk<BC> &walk, int nn, int nm, int lc, bool rev,
                                                     const T *__restrict__ u, const T *__restrict__ v,
                                                     int bar_id, const Coef<T> &p) {
     constexpr int V = Vec<T>::N;
@@ -58,14 +60,14 @@ __device__ __forceinline__ void split_producer_beat(int m, int total, Slice<T> (
     if (m > total) return;  // beyond the last beat: no work and no barrier (same m for both warps)
     if (m < total) {
         if (m + kRing - 1 < total) {
-            ring_issue(ring, m + kRing - 1, g_issue, nm, lc, u, v);
-            g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+            ring_issue(ring, m + kRing - 1, walk.g, nm, lc, u, v);
+            walk.next(nn);
         }
         cp_async_commit();
         cp_async_wait<kRing - 1>();
         const int lane = threadIdx.x & 31;
         Slice<T> cur;
-        ring_read(ring, m, cur);
+        ring_read_bc<T, BC>(ring, m % kRing, rev, cur);
 #pragma unroll
         for (int s = 0; s < K1; ++s) {
             if (s < ACT) {
@@ -137,15 +139,15 @@ __device__ __forceinline__ void split_consumer_beat(int m, int total, Slice<T> (
 }
 
 // Fill beats 0 .. F-1 of the producer: ACT = min(M / 2, K1).
-template <typename T, int K1, int RX, int M, int F>
+template <typename T, int K1, int RX, int BC, int M, int F>
 __device__ __forceinline__ void split_producer_fill(int total, Slice<T> (&W)[3][K1], const RowRing<T> &ring,
-                                                    const Handoff<T> &hand, int &g_issue, int nn, int nm,
-                                                    int lc, const T *__restrict__ u, const T *__restrict__ v,
-                                                    int bar_id, const Coef<T> &p) {
-    split_producer_beat<T, K1, RX, M % 3, (M / 2 < K1 ? M / 2 : K1)>(M, total, W, ring, hand, g_issue, nn, nm,
-                                                                     lc, u, v, bar_id, p);
+                                                    const Handoff<T> &hand, RowWalk<BC> &walk, int nn, int nm,
+                                                    int lc, bool rev, const T *__restrict__ u,
+                                                    const T *__restrict__ v, int bar_id, const Coef<T> &p) {
+    split_producer_beat<T, K1, RX, BC, M % 3, (M / 2 < K1 ? M / 2 : K1)>(M, total, W, ring, hand, walk, nn, nm,
+                                                                         lc, rev, u, v, bar_id, p);
     if constexpr (M + 1 < F)
-        split_producer_fill<T, K1, RX, M + 1, F>(total, W, ring, hand, g_issue, nn, nm, lc, u, v, bar_id, p);
+        split_producer_fill<T, K1, RX, BC, M + 1, F>(total, W, ring, hand, walk, nn, nm, lc, rev, u, v, bar_id, p);
 }
 
 // Fill beats 0 .. F-1 of the consumer (equivalent beat M - 1): local stage j
@@ -164,7 +166,7 @@ __device__ __forceinline__ void split_consumer_fill(int total, Slice<T> (&W)[3][
 }
 
 // One work item per warp pair; `item` is the same for both warps of a pair.
-template <typename T, int K, int RX>
+template <typename T, int K, int RX, int BC>
 __device__ __forceinline__ void temporal_split_item(int item, int bands, const T *__restrict__ u,
                                                     const T *__restrict__ v, T *__restrict__ un,
                                                     T *__restrict__ vn, int nn, int nm, int rows,
@@ -181,7 +183,7 @@ __device__ __forceinline__ void temporal_split_item(int item, int bands, const T
     const int warp = threadIdx.x >> 5;
     const int pair = warp >> 1;
     const int bar_id = 1 + pair;
-    const StripGeom geo = strip_geom<T, K, H>(item % bands, item / bands, nn, nm, rows);
+    const StripGeom geo = strip_geom<T, K, H, BC>(item % bands, item / bands, nn, nm, rows);
     Handoff<T> hand;
     hand.slot = hand_mem[pair];
     if ((warp & 1) == 0) {
@@ -192,23 +194,25 @@ __device__ __forceinline__ void temporal_split_item(int item, int bands, const T
             for (int s = 0; s < K1; ++s) zero_slice(W[a][s]);
         RowRing<T> ring;
         ring.slot = ring_mem[pair];
-        int g_issue = wrap_row((int64_t)geo.r0 - K, nn);
+        RowWalk<BC> walk;
+        walk.start((int64_t)geo.r0 - K, nn);
 #pragma unroll
         for (int j = 0; j < kRing - 1; ++j) {
             if (j < geo.total) {
-                ring_issue(ring, j, g_issue, nm, geo.lc, u, v);
-                g_issue = (g_issue + 1 == nn) ? 0 : g_issue + 1;
+                ring_issue(ring, j, walk.g, nm, geo.lc, u, v);
+                walk.next(nn);
             }
             cp_async_commit();
         }
-        split_producer_fill<T, K1, RX, 0, kFill>(geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v, bar_id, p);
+        split_producer_fill<T, K1, RX, BC, 0, kFill>(geo.total, W, ring, hand, walk, nn, nm, geo.lc, geo.rev, u, v,
+                                                     bar_id, p);
         for (int m = kFill; m <= geo.total; m += 3) {
-            split_producer_beat<T, K1, RX, kFill % 3>(m, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc, u, v,
-                                                      bar_id, p);
-            split_producer_beat<T, K1, RX, (kFill + 1) % 3>(m + 1, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc,
-                                                            u, v, bar_id, p);
-            split_producer_beat<T, K1, RX, (kFill + 2) % 3>(m + 2, geo.total, W, ring, hand, g_issue, nn, nm, geo.lc,
-                                                            u, v, bar_id, p);
+            split_producer_beat<T, K1, RX, BC, kFill % 3>(m, geo.total, W, ring, hand, walk, nn, nm, geo.lc, geo.rev,
+                                                          u, v, bar_id, p);
+            split_producer_beat<T, K1, RX, BC, (kFill + 1) % 3>(m + 1, geo.total, W, ring, hand, walk, nn, nm, geo.lc,
+                                                                geo.rev, u, v, bar_id, p);
+            split_producer_beat<T, K1, RX, BC, (kFill + 2) % 3>(m + 2, geo.total, W, ring, hand, walk, nn, nm, geo.lc,
+                                                                geo.rev, u, v, bar_id, p);
         }
         cp_async_wait<0>();
     } else {

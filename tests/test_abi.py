@@ -239,7 +239,9 @@ def test_plan_resolves_without_running(lib, L):
     lib.rdcnn_destroy(h)
     h = _create(lib, L, nn=64, nm=64, boundary=L.BC_ZEROFLUX)[1]
     var = ctypes.c_int(L.VARIANT_TEMPORAL2)
-    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(L.Tune(4, 0))) == L.EINVAL
+    t4 = L.Tune(4, 0)
+    assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(t4)) == 0  # every model, FP32 / FP64
+    assert var.value == L.VARIANT_TEMPORAL2 and t4.k == 4 and t4.rows >= 1
     lib.rdcnn_destroy(h)
 
 

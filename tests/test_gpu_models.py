@@ -44,6 +44,7 @@ def _variants(nm, dtype):
     out = [("generic", 0)]
     if nm % vec == 0:
         out += [("step1", 0)] + [("temporal", k) for k in ((1, 2, 3, 5, 8) if dtype == F32 else (1, 2, 3, 4))]
+        out += [("temporal2", k) for k in ((2, 5, 8) if dtype == F32 else (2, 4))]
     if dtype == F32 and nm % 8 == 0:
         out += [("temporal_wide", 2), ("temporal_wide", 4)]
     return out
@@ -89,7 +90,7 @@ def test_models_several_tiles_and_launches(rd, oracle_mod, model):
     x, y = f32(x), f32(y)
     T = 61
     ref_u, ref_v = _oracle(oracle_mod, reaction, boundary, x, y, T)
-    for variant, k in (("temporal", 8), ("temporal", 6), ("step1", 0)):
+    for variant, k in (("temporal", 8), ("temporal", 6), ("step1", 0), ("temporal2", 8), ("temporal2", 3)):
         u, v = gpu_run(rd, x, y, _gene(reaction), T, F32, variant, k, reaction=reaction, boundary=boundary,
                        rows=16)
         assert normwise(u, ref_u) <= TOL[F32] and normwise(v, ref_v) <= TOL[F32], (variant, k)
@@ -117,16 +118,9 @@ def test_zero_flux_corners_at_full_size(rd, oracle_mod, reaction):
             assert normwise(gu, ref_u[r, c]) <= TOL[F32] and normwise(gv, ref_v[r, c]) <= TOL[F32]
 
 
-def test_temporal2_and_adjoint_reject_the_variants(rd):
-    x = torch.zeros((16, 16), device="cuda")
-    g = rd.Grid(16, 16, None, dtype=F32, boundary="zeroflux")
-    g.set_state(x, x)
-    with pytest.raises(rd.RDCNNError):
-        g.run(8, variant="temporal2", k=4)
-    with pytest.raises(rd.RDCNNError):
-        g.adjoint(4, x, x, x, x)
-    g.close()
-    g = rd.Grid(16, 16, CENN_GENE, dtype=F32, reaction="cenn")
+def test_temporal2_rejects_16bit_planes(rd):
+    x = torch.zeros((16, 16), device="cuda", dtype=torch.bfloat16)
+    g = rd.Grid(16, 16, None, dtype=torch.bfloat16, boundary="zeroflux")
     g.set_state(x, x)
     with pytest.raises(rd.RDCNNError):
         g.run(8, variant="temporal2", k=4)
