@@ -295,3 +295,32 @@ def test_cenn_autograd_fit_step(rd):
         th2 = theta - 1e-2 * theta.grad / theta.grad.norm()
     u2, _ = rd.RDCNNFunction.apply(x, w, th2, T, 0.1, 0, "periodic", "cenn")
     assert torch.mean((u2 - target) ** 2).item() < loss.item()
+
+
+@pytest.mark.parametrize("dtype,k", [(F32, 2), (F32, 5), (F32, 8), (F64, 1), (F64, 3), (F64, 4)],
+                         ids=["f32-k2", "f32-k5", "f32-k8", "f64-k1", "f64-k3", "f64-k4"])
+@pytest.mark.parametrize("model", [("fhn", "periodic"), ("fhn", "zeroflux"), ("cenn", "zeroflux")])
+def test_adjoint_depths_match_oracle(rd, oracle_mod, dtype, k, model):
+    """The handle's tune k sets the recompute / reverse depth (one halo lane while k <= V, two
+    above); every depth gives the oracle's adjoint (T not a multiple of k: ragged launches)."""
+    reaction, boundary = model
+    nn, nm, T = 40, 64, 27
+    gene = CENN_ADJ if reaction == "cenn" else inp.default_params(Du=0.12, Dv=0.3)
+    scale = 1.7 if reaction == "cenn" else 1.0
+    x = scale * inp.uniform_field(91, nn, nm)
+    y = inp.uniform_field(92, nn, nm)
+    wu = inp.uniform_field(93, nn, nm) / (nn * nm)
+    wv = inp.uniform_field(94, nn, nm) / (nn * nm)
+    if dtype == F32:
+        x, y, wu, wv = f32(x), f32(y), f32(wu), f32(wv)
+    g = rd.Grid(nn, nm, gene, dtype=dtype, reaction=reaction, boundary=boundary)
+    g.set_tune(k=k)
+    du, dv, gp = g.adjoint(T, _dev(x, dtype), _dev(y, dtype), _dev(wu, dtype), _dev(wv, dtype), 3)
+    torch.cuda.synchronize()
+    rx = oracle_mod.CENN if reaction == "cenn" else oracle_mod.FHN
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    ou, ov, og = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=3, reaction=rx, boundary=bc)
+    tol, gtol = (1e-10, 1e-9) if dtype == F64 else (1e-5, 1e-5)
+    assert normwise(du.double().cpu().numpy(), ou) <= tol and normwise(dv.double().cpu().numpy(), ov) <= tol
+    got = np.array([gp[n] for n in NAMES])
+    np.testing.assert_allclose(got, og, rtol=gtol, atol=gtol * np.linalg.norm(og))
