@@ -7,8 +7,6 @@
 // units so that they compile in parallel.
 #pragma once
 
-#include <type_traits>
-
 #include "common.cuh"
 #include "internal.h"
 #include "temporal.cuh"
