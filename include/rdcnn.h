@@ -45,8 +45,9 @@
  *  - Memory ownership: the CALLER owns every buffer, host or device.  The
  *    library allocates no device buffers; scratch space is passed in by the
  *    caller, sized by the matching *_workspace_bytes query.  A handle creates
- *    only CUDA objects of its own (streams for snapshot copies and graph
- *    capture, one graph executable), released by rdcnn_destroy.
+ *    only CUDA objects of its own (streams for snapshot copies, graph
+ *    capture and the adjoint's segment rebuilds, a few events, one graph
+ *    executable), released by rdcnn_destroy.
  *  - Streams: work is enqueued on the caller's CUDA stream (cudaStream_t
  *    passed as void*; NULL = legacy default stream).  Calls that return data
  *    to host memory synchronise that stream before returning; all other calls
@@ -307,7 +308,11 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
  * its reaction: for CENN handles grad holds dL/dDu (the neighbour feedback
  * weight) and dL/dc (the self-feedback weight), the other entries are 0, and
  * the output function's slope is taken as 1 on (-1, 1) and 0 elsewhere.
- * Synchronises the handle's stream (grad is a host result). */
+ * With more than one checkpoint segment the segment rebuilds run on a
+ * stream the handle owns (created on first use, released by rdcnn_destroy),
+ * ordered against the bound stream by events, and the workspace holds two
+ * sets of segment states.  Synchronises the handle's stream (grad is a host
+ * result). */
 int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
                   const void *dLdu_T, const void *dLdv_T, int64_t n_checkpoints,
                   void *dLdu0, void *dLdv0, double grad[6],

@@ -32,9 +32,13 @@
 // steps).  Segments are then processed last to first: k_forward_all rebuilds
 // the segment's states K per launch (every stage of the temporal pipeline is
 // stored), and k_adjoint_pipe walks them backwards K steps per launch with
-// the same register pipeline running the co-state update.  Each warp owns
-// the same cells at every launch and adds its sums to its own FP64 slot, so
-// the gradient is deterministic.
+// the same register pipeline running the co-state update.  With more than
+// one segment the rebuilds run on a second stream into two alternating
+// buffer sets, so the rebuild of segment s - 1 overlaps the reverse sweep of
+// segment s (events order each rebuild after the reverse sweep that last read
+// its set, and each reverse sweep after its rebuild).  Each warp owns the
+// same cells at every launch and adds its sums to its own FP64 slot, so the
+// gradient is deterministic.
 #include <algorithm>
 #include <cmath>
 
@@ -130,7 +134,7 @@ cudaError_t forward_all_launch(int reaction, int boundary, int k, int H, const v
 }
 
 struct AdjLayout {
-    int64_t S, nseg, nslots;
+    int64_t S, nseg, nslots, nsets;  // nsets: segment buffer sets (2 when segments can overlap)
     int ka, H;  // depth of the recompute / reverse launches, halo lanes of the warp map
     size_t plane, ck_off, seg_off, lam_off, part_off, out_off, total;
 };
@@ -144,26 +148,53 @@ AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck, 
     L.S = (std::max<int64_t>(T, 1) + nck - 1) / nck;
     L.nseg = (std::max<int64_t>(T, 1) + L.S - 1) / L.S;
     L.nslots = std::max<int64_t>(L.S, 2);
+    L.nsets = L.nseg > 1 ? 2 : 1;
     L.plane = (((size_t)nn * nm * elem_size(dtype)) + 255) & ~(size_t)255;
     const PipeShape sh = pipe_shape(dtype, nn, nm, L.H);
     L.ck_off = 0;
     L.seg_off = L.ck_off + (size_t)L.nseg * 2 * L.plane;
-    L.lam_off = L.seg_off + (size_t)L.nslots * 2 * L.plane;
+    L.lam_off = L.seg_off + (size_t)L.nsets * L.nslots * 2 * L.plane;
     L.part_off = L.lam_off + 4 * L.plane;
     L.out_off = L.part_off + (((size_t)sh.nwarps * 6 * sizeof(double) + 255) & ~(size_t)255);
     L.total = L.out_off + 256;
     return L;
 }
 
+// The second stream and events of the overlapped driver (created once per
+// handle); false if they cannot be had, and the driver then runs on one stream.
+bool adj_streams(rdcnn_t *h) {
+    if (!h->adj_stream && cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->adj_stream = nullptr;
+        return false;
+    }
+    for (cudaEvent_t &ev : h->adj_ev) {
+        if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ev = nullptr;
+            return false;
+        }
+    }
+    return true;
+}
+
 template <typename T>
-int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary, cudaStream_t s,
-              int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T, const void *dLdv_T,
-              const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
+int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary,
+              cudaStream_t s, int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T,
+              const void *dLdv_T, const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
     const size_t bytes = (size_t)nn * nm * sizeof(T);
     auto ck_u = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i) * L.plane); };
     auto ck_v = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i + 1) * L.plane); };
-    auto seg_u = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * i) * L.plane); };
-    auto seg_v = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * i + 1) * L.plane); };
+    int set = 0;  // buffer set of the segment being rebuilt / swept
+    auto seg_u = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * (set * L.nslots + i)) * L.plane); };
+    auto seg_v = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * (set * L.nslots + i) + 1) * L.plane); };
+    const bool overlap = L.nsets == 2 && adj_streams(h);
+    cudaStream_t rs = overlap ? h->adj_stream : s;  // the rebuild stream
+    // an error after work went to the rebuild stream: let it drain before returning
+    auto fail = [&](cudaError_t err, const char *what) {
+        if (overlap) (void)cudaStreamSynchronize(rs);
+        return cuda_error(err, what);
+    };
     T *lam_u[2] = {(T *)(ws + L.lam_off), (T *)(ws + L.lam_off + 2 * L.plane)};
     T *lam_v[2] = {(T *)(ws + L.lam_off + L.plane), (T *)(ws + L.lam_off + 3 * L.plane)};
     double *partial = (double *)(ws + L.part_off);
@@ -193,19 +224,34 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             cu = nu; cv = nv;
         }
     }
+    if (overlap) {  // the rebuilds read the checkpoints
+        e = cudaEventRecord(h->adj_ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, h->adj_ev[0], 0);
+        if (e != cudaSuccess) return fail(e, "adjoint stream order");
+    }
     // segments last to first: rebuild the states, then sweep the co-state back
     int cur = 0;
     for (int64_t sg = L.nseg - 1; sg >= 0 && nsteps > 0; --sg) {
         const int64_t len = std::min<int64_t>(L.S, nsteps - sg * L.S);
+        set = overlap ? (int)((L.nseg - 1 - sg) & 1) : 0;
         auto state_u = [&](int64_t q) { return q == 0 ? ck_u(sg) : seg_u(q); };
         auto state_v = [&](int64_t q) { return q == 0 ? ck_v(sg) : seg_v(q); };
+        if (overlap && sg + 2 <= L.nseg - 1) {  // the reverse sweep two segments back read this set
+            e = cudaStreamWaitEvent(rs, h->adj_ev[3 + set], 0);
+            if (e != cudaSuccess) return fail(e, "adjoint stream order");
+        }
         for (int64_t q = 0; q + 1 < len;) {
             const int kk = (int)std::min<int64_t>(ka, len - 1 - q);
             StagePlanes<T> pl{};
             for (int j = 0; j < kk; ++j) { pl.u[j] = seg_u(q + 1 + j); pl.v[j] = seg_v(q + 1 + j); }
-            e = forward_all_launch<T>(reaction, boundary, kk, L.H, state_u(q), state_v(q), pl, nn, nm, sh, p, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint recompute");
+            e = forward_all_launch<T>(reaction, boundary, kk, L.H, state_u(q), state_v(q), pl, nn, nm, sh, p, rs);
+            if (e != cudaSuccess) return fail(e, "adjoint recompute");
             q += kk;
+        }
+        if (overlap) {
+            e = cudaEventRecord(h->adj_ev[1 + set], rs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->adj_ev[1 + set], 0);
+            if (e != cudaSuccess) return fail(e, "adjoint stream order");
         }
         for (int64_t qh = len; qh > 0;) {
             const int kk = (int)std::min<int64_t>(ka, qh);
@@ -213,9 +259,13 @@ int adjoint_t(int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reac
             for (int j = 0; j < kk; ++j) { st.u[j] = state_u(qh - 1 - j); st.v[j] = state_v(qh - 1 - j); }
             e = reverse_launch<T>(reaction, boundary, kk, L.H, lam_u[cur], lam_v[cur], lam_u[cur ^ 1], lam_v[cur ^ 1], st,
                                   partial, nn, nm, sh, p, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint reverse step");
+            if (e != cudaSuccess) return fail(e, "adjoint reverse step");
             cur ^= 1;
             qh -= kk;
+        }
+        if (overlap) {
+            e = cudaEventRecord(h->adj_ev[3 + set], s);
+            if (e != cudaSuccess) return fail(e, "adjoint stream order");
         }
     }
     k_reduce_partials<<<1, 256, 0, s>>>(partial, sh.nwarps, p.dt, gout);
@@ -271,9 +321,9 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     if (workspace_bytes < L.total)
         return set_error(RDCNN_ESPACE, "adjoint workspace has %zu bytes, need %zu", workspace_bytes, L.total);
     if (dtype == RDCNN_F64)
-        return adjoint_t<double>(nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
+        return adjoint_t<double>(h, nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
                                  (char *)workspace, dLdu0, dLdv0, grad);
-    return adjoint_t<float>(nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
+    return adjoint_t<float>(h, nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
                             (char *)workspace, dLdu0, dLdv0, grad);
 }
 

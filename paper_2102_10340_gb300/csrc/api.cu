@@ -399,6 +399,9 @@ void rdcnn_destroy(rdcnn_t *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
+    for (cudaEvent_t ev : h->adj_ev)
+        if (ev) cudaEventDestroy(ev);
     delete h;
 }
 

@@ -20,6 +20,11 @@ struct rdcnn {
     bool bound = false;
     int tune_k = 0, tune_rows = 0;
     cudaStream_t copy_stream = nullptr;  // created on first use by rdcnn_run_snapshots
+    // rdcnn_adjoint's second stream (segment rebuilds overlap the reverse
+    // sweep) and its events: [0] checkpoints ready, [1..2] rebuild of buffer
+    // set 0 / 1 done, [3..4] reverse over set 0 / 1 done.  Created on first use.
+    cudaStream_t adj_stream = nullptr;
+    cudaEvent_t adj_ev[5] = {};
     // Graph replay of runs of small grids (run_core): a captured sequence of
     // full-depth launches and what it was captured for.
     cudaStream_t capture_stream = nullptr;
