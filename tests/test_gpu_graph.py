@@ -63,3 +63,30 @@ def test_graph_follows_gene_shape_and_model_changes(rd):
     assert torch.equal(z.u, w.u) and torch.equal(z.v, w.v)
     for h in (g, ref, z, w):
         h.close()
+
+
+@pytest.mark.parametrize("variant,k", [("temporal", 4), ("step1", 0), ("temporal2", 6)])
+def test_run_captured_into_a_caller_graph(rd, variant, k):
+    """rdcnn_run inside the caller's own stream capture (torch.cuda.graph): the library skips
+    its graph replay, records its programmatically serialised launches into the caller's
+    graph, and replaying that graph twice equals two direct runs, bit for bit."""
+    x = inp.uniform_field(21, 96, 128)
+    T = 3 * 64 * 4 + 6  # long enough for the library's own graph path outside a capture
+    a = _grid(rd, x, None)
+    a.run(8, variant=variant, k=k)  # warm-up outside the capture (module load, shape queries)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", torch.float32)
+    a.set_state(xt, 0.5 * xt)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        a.run(T, variant=variant, k=k)
+    torch.cuda.synchronize()
+    assert torch.equal(a.u, xt)  # capturing runs nothing
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    b = _grid(rd, x, None)
+    b.run(T, variant=variant, k=k)
+    b.run(T, variant=variant, k=k)
+    torch.cuda.synchronize()
+    assert torch.equal(a.u, b.u) and torch.equal(a.v, b.v)
