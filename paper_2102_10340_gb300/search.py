@@ -85,3 +85,10 @@ def du_dv_grid(du_values, dv_values, base: dict | None = None) -> list:
     """Genes on a (Du, Dv) grid around ``base`` (default: the paper's defaults)."""
     base = dict(base or rd.DEFAULT_PARAMS)
     return [dict(base, Du=float(du), Dv=float(dv)) for du in du_values for dv in dv_values]
+
+
+def ab_grid(a_values, b_values, base: dict | None = None) -> list:
+    """Genes on an (a, b) grid around ``base``: the plane Sec. III.B searches for
+    image-processing (edge-detecting) behaviour."""
+    base = dict(base or rd.DEFAULT_PARAMS)
+    return [dict(base, a=float(a), b=float(b)) for a in a_values for b in b_values]

@@ -29,3 +29,12 @@ def test_du_dv_grid():
     g = search.du_dv_grid([0.3, 0.5], [0.8, 1.0])
     assert [(x["Du"], x["Dv"]) for x in g] == [(0.3, 0.8), (0.3, 1.0), (0.5, 0.8), (0.5, 1.0)]
     assert all(x["a"] == -0.3 and x["dt"] == 0.1 for x in g)
+
+
+def test_ab_grid():
+    from paper_2102_10340_gb300 import search
+
+    g = search.ab_grid([-0.3, 0.0], [1.0, 1.3], base={"dt": 0.05, "a": 9.0, "b": 9.0, "eps": -0.1, "c": 1.0,
+                                                      "Du": 0.06, "Dv": 1.0})
+    assert [(x["a"], x["b"]) for x in g] == [(-0.3, 1.0), (-0.3, 1.3), (0.0, 1.0), (0.0, 1.3)]
+    assert all(x["dt"] == 0.05 and x["Du"] == 0.06 for x in g)
