@@ -671,6 +671,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if (N, T) == (N_GRID, T_STEPS) else f"{N}x{N} FP32 patch, T={T}",
                        "grid": [N, N], "T": T, "variant": variant, "k": k, "rows": plan["rows"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "launch": "programmatic dependent launch" if os.environ.get("RDCNN_PDL", "1")[:1] != "0"
+                                 else "plain launches (RDCNN_PDL=0)",
                        "l2": "inputs larger than L2: 4 x 64 MiB planes (state + ping-pong) vs 126 MiB L2",
                        "vs_baseline_ref": "Table I PyCUDA 14545 Mcell/s at N=4096, Tesla P100 (context)"},
             "e2e": {"value": e2e_value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 4 * N * N,
