@@ -34,7 +34,9 @@ Functions and the passages they follow:
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (fixed point, linearisation, Fourier decay, mass conservation, symmetries,
-hand-expanded tiny grids, finite differences).  None is "parity unpinned".
+hand-expanded tiny grids, finite differences; :func:`init_state` by products
+worked by hand for k_a = 0.75 and -2.5 and by the uncoupled-cell map from
+k_a x).  None is "parity unpinned".
 """
 from __future__ import annotations
 

@@ -138,7 +138,7 @@ def test_zero_steps_and_state_roundtrip(rd):
 def test_init_from_host_and_device(rd, oracle_mod):
     x = f32(inp.uniform_field(12, 32, 64))
     ka = 0.75
-    ref = oracle_mod.run(*oracle_mod.init_state(f32(ka * x), 1.0), inp.default_params(), 10)
+    ref = oracle_mod.run(*oracle_mod.init_state(x, ka), inp.default_params(), 10)
     for src in (torch.from_numpy(x).float(), torch.from_numpy(x).float().cuda()):
         g = rd.Grid(32, 64, inp.default_params(), dtype=F32)
         g.init(src, ka).run(10)

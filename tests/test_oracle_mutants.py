@@ -3,12 +3,15 @@
 Each case below plants one mistake in a copy of ``oracle/rdcnn_oracle.c``
 (on the CPU, in a temporary directory), compiles it, and runs every pin of
 ``test_oracle_pins.py`` against the mutant.  At least one pin must fail.
+The Python-side cases replace ``init_state`` (u = v = k_a x) on an oracle
+object with a planted mistake in the same way.
 """
 import inspect
 import os
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 import oracle
@@ -79,6 +82,51 @@ def mutant_dir(tmp_path_factory):
     return tmp_path_factory.mktemp("oracle_mutants")
 
 
+# Mistakes planted in the Python side of the oracle (init_state, Eq. 1 first line):
+# each replaces the function on an oracle object that otherwise uses the real C library.
+def _init_v_unscaled(x, ka=1.0):
+    x = np.asarray(x, dtype=np.float64)
+    return ka * x, x.copy()
+
+
+def _init_ka_squared(x, ka=1.0):
+    x = np.asarray(x, dtype=np.float64)
+    return ka * ka * x, ka * ka * x
+
+
+def _init_ka_ignored(x, ka=1.0):
+    x = np.asarray(x, dtype=np.float64)
+    return x.copy(), x.copy()
+
+
+def _init_shared_plane(x, ka=1.0):
+    u = ka * np.asarray(x, dtype=np.float64)
+    return u, u
+
+
+PY_MUTANTS = {"init_v_unscaled": _init_v_unscaled, "init_ka_squared": _init_ka_squared,
+              "init_ka_ignored": _init_ka_ignored, "init_shared_plane": _init_shared_plane}
+
+
+def _caught_by_pins(bad):
+    caught = []
+    for fn, kwargs in _pin_cases():
+        if "oracle_mod" not in inspect.signature(fn).parameters:
+            continue
+        try:
+            fn(oracle_mod=bad, **kwargs)
+        except (AssertionError, RuntimeError, ValueError):
+            caught.append(fn.__name__)
+    return caught
+
+
+@pytest.mark.parametrize("mutant", sorted(PY_MUTANTS))
+def test_pins_reject_python_mutant(mutant):
+    bad = oracle.Oracle(oracle.build())
+    bad.init_state = PY_MUTANTS[mutant]
+    assert _caught_by_pins(bad), f"no pin caught mutant {mutant}"
+
+
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
 def test_pins_reject_mutant(mutant, mutant_dir):
     before, after = MUTANTS[mutant]
@@ -89,12 +137,4 @@ def test_pins_reject_mutant(mutant, mutant_dir):
     lib = str(mutant_dir / f"{mutant}.so")
     oracle.compile_source(str(src), lib)
     bad = oracle.Oracle(lib)
-    caught = []
-    for fn, kwargs in _pin_cases():
-        if "oracle_mod" not in inspect.signature(fn).parameters:
-            continue
-        try:
-            fn(oracle_mod=bad, **kwargs)
-        except (AssertionError, RuntimeError, ValueError):
-            caught.append(fn.__name__)
-    assert caught, f"no pin caught mutant {mutant}"
+    assert _caught_by_pins(bad), f"no pin caught mutant {mutant}"

@@ -108,14 +108,39 @@ def test_uniform_stays_uniform_and_follows_cell_map(oracle_mod):
     assert ut[0, 0] == su[-1] and vt[0, 0] == sv[-1]
 
 
-def test_no_diffusion_means_independent_cells(oracle_mod):
+# u = v = k_a x (Eq. 1, first line) on a 2 x 3 image, the products worked by hand
+# (every factor and product is a short binary fraction, so FP64 holds them exactly).
+INIT_X = [[1.0, -2.0, 0.5], [4.0, -0.25, 3.0]]
+INIT_CASES = {
+    0.75: [[0.75, -1.5, 0.375], [3.0, -0.1875, 2.25]],
+    -2.5: [[-2.5, 5.0, -1.25], [-10.0, 0.625, -7.5]],
+}
+
+
+@pytest.mark.parametrize("ka", sorted(INIT_CASES))
+def test_init_state_scales_both_fields_by_ka(oracle_mod, ka):
+    x = np.array(INIT_X)
+    u, v = oracle_mod.init_state(x, ka)
+    want = np.array(INIT_CASES[ka])
+    assert u.dtype == np.float64 and v.dtype == np.float64
+    assert u.shape == (2, 3) and v.shape == (2, 3)
+    assert np.array_equal(u, want) and np.array_equal(v, want)
+    # two independent planes, neither of them the input image
+    assert not np.shares_memory(u, v)
+    assert not np.shares_memory(u, x) and not np.shares_memory(v, x)
+    u[0, 0] = 99.0
+    assert v[0, 0] == want[0, 0] and x[0, 0] == INIT_X[0][0]
+
+
+@pytest.mark.parametrize("ka", [1.0, 0.6])
+def test_no_diffusion_means_independent_cells(oracle_mod, ka):
     gene = inp.default_params(Du=0.0, Dv=0.0)
     x = inp.uniform_field(0, 5, 6)
-    u, v = oracle_mod.init_state(x, 1.0)
+    u, v = oracle_mod.init_state(x, ka)
     ut, vt = oracle_mod.run(u, v, gene, 100)
     for i in range(5):
         for j in range(6):
-            su, sv = oracle_mod.scalar_map(x[i, j], x[i, j], gene, 100)
+            su, sv = oracle_mod.scalar_map(ka * x[i, j], ka * x[i, j], gene, 100)
             assert ut[i, j] == su[-1] and vt[i, j] == sv[-1]
 
 
