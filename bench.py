@@ -518,11 +518,83 @@ def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
     g.set_state(x, x).run(T)
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
+    g.close()
     return {"grid": [N, N], "T": T, "checkpoints": int(np.ceil(np.sqrt(T))), "adjoint_ms": t_adj * 1e3,
             "plain_fwd_ms": t_fwd * 1e3, "adjoint_over_fwd": t_adj / t_fwd,
             "value": N * N * T / t_adj / 1e9, "unit": "Gcell-updates/s (forward steps differentiated)",
             "all_states": {"checkpoints": 1, "adjoint_ms": t_all * 1e3, "adjoint_over_fwd": t_all / t_fwd,
-                           "workspace_bytes": int(all_bytes)}}
+                           "workspace_bytes": int(all_bytes)},
+            "gradient_check": adjoint_gradient_check(rd, torch, N=N, T=T)}
+
+
+def adjoint_gradient_check(rd, torch, N=512, T=2000, h_state=1e-4, h_gene=1e-5, quick=False):
+    """Accuracy of the adjoint's gradients on the adjoint workload (N x N, T steps, loss
+    L = mean((u_T - target)^2), target the seeded +-1 checkerboard of period 32), for the FP32
+    and the FP64 kernels, against FP64 central differences.
+
+    The differences run the FP64 forward kernels (themselves held to the oracle at 1e-12
+    normwise by the parity tests): dL/du0 and dL/dv0 are checked as directional derivatives
+    along seeded U[-1, 1] directions (steps h and 2h, to show the difference quotient has
+    converged), the six gene entries one by one (step h_gene * |p|) and as a vector.  Both
+    adjoints start from the same FP32-rounded x, so their errors are comparable."""
+    if quick:
+        T = 200
+    p = inp.default_params()
+    x = torch.from_numpy(np.asarray(inp.uniform_field(0, N, N), dtype=np.float32).astype(np.float64)).cuda()
+    tgt = torch.from_numpy(inp.checkerboard(0, N, N)).cuda()
+    du = torch.from_numpy(inp.uniform_field(101, N, N)).cuda()
+    dv = torch.from_numpy(inp.uniform_field(102, N, N)).cuda()
+    g64 = rd.Grid(N, N, p, dtype=torch.float64)
+
+    def loss(u0, v0, params=None):
+        if params is not None:
+            g64.set_params(params)
+        g64.set_state(u0.contiguous(), v0.contiguous()).run(T)
+        val = float(torch.mean((g64.u - tgt) ** 2))
+        if params is not None:
+            g64.set_params(p)
+        return val
+
+    def central(fn, h):
+        return (fn(h) - fn(-h)) / (2.0 * h)
+
+    fd = {}
+    for name, d in (("u0", du), ("v0", dv)):
+        if name == "u0":
+            f = lambda h, d=d: loss(x + h * d, x)  # noqa: E731
+        else:
+            f = lambda h, d=d: loss(x, x + h * d)  # noqa: E731
+        fd[name] = (central(f, h_state), central(f, 2 * h_state))
+    fd_gene = []
+    for name in rd.GRAD_NAMES:
+        step = h_gene * max(abs(p[name]), 1e-3)
+
+        def f(h, name=name):
+            q = dict(p)
+            q[name] = p[name] + h
+            return loss(x, x, q)
+        fd_gene.append(central(f, step))
+    fd_gene = np.array(fd_gene)
+
+    out = {"grid": [N, N], "T": T, "loss": "mean((u_T - target)^2), target +-1 checkerboard, period 32",
+           "reference": "FP64 central differences of the FP64 forward kernels",
+           "h_state": h_state, "h_gene_rel": h_gene,
+           "fd_converged": {k: abs(a - b) / abs(a) for k, (a, b) in fd.items()}}
+    for tag, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        g = rd.Grid(N, N, p, dtype=dt)
+        xs = x.to(dt)
+        g.set_state(xs, xs).run(T)
+        gu = (2.0 * (g.u.double() - tgt) / g.u.numel()).to(dt).contiguous()
+        du0, dv0, gp = g.adjoint(T, xs, xs, gu, torch.zeros_like(gu))
+        ad = {"u0": float(torch.sum(du0.double() * du)), "v0": float(torch.sum(dv0.double() * dv))}
+        gv = np.array([gp[k] for k in rd.GRAD_NAMES])
+        res = {f"dLd{k}_dir_rel_err": abs(ad[k] - fd[k][0]) / abs(fd[k][0]) for k in ("u0", "v0")}
+        res["gene_rel_err"] = float(np.linalg.norm(gv - fd_gene) / np.linalg.norm(fd_gene))
+        res["gene_entry_rel_err"] = {k: float(abs(a - b) / abs(b)) for k, a, b in zip(rd.GRAD_NAMES, gv, fd_gene)}
+        out[tag] = res
+        g.close()
+    g64.close()
+    return out
 
 
 def run_ours(args):
@@ -601,6 +673,7 @@ def run_ours(args):
         return 0
 
     peaks = load_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # roofline of the dominant kernel (one launch advances k steps over the whole grid)
     fused = variant in ("temporal", "temporal2", "temporal_wide")
     k = tune["k"] if fused else 1
@@ -613,8 +686,8 @@ def run_ours(args):
     cells = N * N
     if fused and k > 1:
         flops = FLOPS_PER_CELL_STEP * cells * k
-        # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-        peak_tf = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        # FP32 FMA peak: SMs x 128 lanes x 2 flop x max SM clock
+        peak_tf = n_sm * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = flops / (launch_ms * 1e-3) / 1e12
         kname = {"temporal": "k_temporal", "temporal2": "k_temporal_split",
                  "temporal_wide": "k_temporal_wide"}[variant]
@@ -624,7 +697,7 @@ def run_ours(args):
         inst = profiled_instructions(f"{kname}_f32_k{k}_4096.md") if traffic is not None else None
         if inst:
             # warp-instruction issue: 4 schedulers per SM, one instruction per clock each
-            peak_issue = 152 * 4 * peaks["sm_max_mhz"] * 1e6
+            peak_issue = n_sm * 4 * peaks["sm_max_mhz"] * 1e6
             issue = {"achieved": inst / (launch_ms * 1e-3), "peak": peak_issue, "unit": "warp-inst/s",
                      "frac": inst / (launch_ms * 1e-3) / peak_issue, "instructions_per_launch": inst,
                      "source": tsrc}
@@ -632,7 +705,7 @@ def run_ours(args):
                     "issue": issue,
                     "traffic": traffic, "traffic_source": tsrc,
                     "algorithmic_bytes": BYTES_PER_CELL_STEP * cells, "kernel": f"{kname}<float,K={k}>",
-                    "peak_source": "152 SM x 128 FP32 lanes x 2 flop x sm_max_mhz "
+                    "peak_source": f"{n_sm} SM (device) x 128 FP32 lanes x 2 flop x sm_max_mhz "
                                    f"({peaks['sm_max_mhz']:.0f} MHz, {peaks['source']})",
                     "launch_ms": launch_ms, "launch_ms_source": "timed region / launches in it",
                     "launch_ms_isolated": launch_ms_isolated,
@@ -680,8 +753,33 @@ def run_ours(args):
             "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
             "single_step_kernel": step1, "cpu_baseline": cpu}
     line.update(extra)
+    line["followon"] = followon_summary(line)  # last key: the compact ratios end the line
     print(json.dumps(line), flush=True)
     return 0
+
+
+def followon_summary(line):
+    """The headline's companion figures in a few hundred bytes: the single-step kernel against
+    the HBM roofline, the batched sweep and the adjoint against plain forward runs, and the
+    adjoint's gradient errors."""
+    out = {"headline_gcell_s": line["value"], "roofline_frac": line["roofline"]["frac"],
+           "single_step": {"gcell_s": line["single_step_kernel"]["gcell_s"],
+                           "frac_hbm": line["single_step_kernel"]["frac"]}}
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"gcell_s": b["value"], "plain_fwd_gcell_s": b["plain_fwd_value"],
+                          "vs_plain_fwd": b["vs_plain_fwd"]}
+    a = line.get("adjoint")
+    if a:
+        out["adjoint"] = {"ms": a["adjoint_ms"], "plain_fwd_ms": a["plain_fwd_ms"],
+                          "adjoint_over_fwd": a["adjoint_over_fwd"],
+                          "all_states_over_fwd": a["all_states"]["adjoint_over_fwd"]}
+        gc = a.get("gradient_check")
+        if gc:
+            for tag in ("fp32", "fp64"):
+                out["adjoint"][f"grad_err_{tag}"] = {k: gc[tag][k] for k in
+                                                     ("dLdu0_dir_rel_err", "dLdv0_dir_rel_err", "gene_rel_err")}
+    return out
 
 
 def main(argv=None):

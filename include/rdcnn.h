@@ -16,7 +16,9 @@
  * The paper presents the simulator as a template for other cellular
  * nonlinear / FDTD models and names the Chua-Yang cellular neural network
  * (Sec. I, Sec. II.A) without fixing a second model.  Two such variants are
- * provided by rdcnn_create / rdcnn_run (forward stepping only):
+ * provided, and every entry point supports them (single-grid runs, the
+ * batched sweep, snapshots and the adjoint) except rdcnn_run_static, which
+ * takes neither:
  *  - RDCNN_BC_ZEROFLUX: no flux across the grid edge; the ghost cell beyond
  *    an edge holds the value of the edge cell itself;
  *  - RDCNN_REACTION_CENN: the Chua-Yang cell with output
@@ -41,7 +43,8 @@
  * Conventions shared by every entry point
  *  - Layout: one plane per field, row-major [NN][NM], element (i, j) at
  *    offset i * NM + j; i is the row (NN rows), j the column (NM columns).
- *  - Element type: float (RDCNN_F32) or double (RDCNN_F64), fixed per handle.
+ *  - Element type: float (RDCNN_F32), double (RDCNN_F64), bfloat16
+ *    (RDCNN_BF16) or IEEE half (RDCNN_F16), fixed per handle.
  *  - Memory ownership: the CALLER owns every buffer, host or device.  The
  *    library allocates no device buffers; scratch space is passed in by the
  *    caller, sized by the matching *_workspace_bytes query.  A handle creates
@@ -119,7 +122,7 @@ typedef struct rdcnn rdcnn_t;                     /* opaque simulation handle */
 /* Create a handle for an NN x NM grid (Sec. II.A: "NNxNM" array of cells).
  * 1 <= nn, nm < 2^30 and nn * nm <= 2^40 (plane offsets are 64-bit; grids
  * beyond 2^31 cells are supported); p finite; boundary RDCNN_BC_PERIODIC/ZEROFLUX; dtype
- * RDCNN_F32/F64; reaction RDCNN_REACTION_FHN/NONE/CENN.  Du, Dv >= 0 except
+ * RDCNN_F32/F64/BF16/F16; reaction RDCNN_REACTION_FHN/NONE/CENN.  Du, Dv >= 0 except
  * for CENN, whose feedback weights c and Du may have either sign (and which
  * gets no RDCNN_WARN_CFL check).  Pure host call (no CUDA work).
  * Returns RDCNN_OK, RDCNN_WARN_CFL (handle still created) or RDCNN_EINVAL.
@@ -330,14 +333,18 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
  * pointers from another component, and so cannot supply the scratch
  * workspace rdcnn_bind asks for.
  *
- * Advances the caller's state planes u, v (device, NN x NM, dtype, updated in
- * place) by T steps of the same update as rdcnn_run (temporal kernel when NM
- * is a multiple of 4 / 2 and u, v are 16-byte aligned, generic otherwise;
- * k = steps per launch, 0 = default), asynchronously on `stream`.  The two
+ * Advances the caller's state planes u, v (device, NN x NM, dtype RDCNN_F32
+ * or RDCNN_F64, updated in place) by T steps of the same update as rdcnn_run
+ * on a periodic (toroidal) handle -- this entry point has no boundary
+ * argument and always uses the paper's torus -- with the FHN or NONE
+ * reaction (temporal kernel when NM is a multiple of 4 / 2 and u, v are
+ * 16-byte aligned, generic otherwise; k = steps per launch, 0 = default;
+ * the same bits as rdcnn_run), asynchronously on `stream`.  The two
  * ping-pong planes live in one file-scope __device__ array of
  * RDCNN_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading this library
  * holds until the process exits, so NN * NM * sizeof(element) may be at most
- * 8 MiB (2,097,152 FP32 or 1,048,576 FP64 cells); larger grids return
+ * 8 MiB (2,097,152 FP32 or 1,048,576 FP64 cells; the second plane starts at
+ * the first one's size rounded up to 256 bytes); larger grids return
  * RDCNN_EINVAL before any GPU work.  The call allocates nothing (no
  * cudaMalloc, cudaFree or allocating library routine).
  * All calls share that one array and it keeps the last call's contents
@@ -346,7 +353,9 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
  * it and must be serialised by the caller.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress, which may load
  * the library's module on that device); make that first call before any
- * stream capture begins on the device.
+ * stream capture begins on the device.  The address is kept for the life of
+ * the process, so the entry point must not be used after a cudaDeviceReset
+ * (or another teardown of the device's primary context) in that process.
  * Errors: RDCNN_EINVAL, RDCNN_ENONFINITE, RDCNN_ECUDA; RDCNN_WARN_CFL as for
  * rdcnn_create. */
 int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, int reaction,

@@ -13,7 +13,11 @@
 //    for the array until the process exits;
 //  - one grid may use at most half of it per plane: NN*NM*sizeof(element)
 //    <= 8 MiB, i.e. 2,097,152 FP32 cells or 1,048,576 FP64 cells; larger
-//    grids are rejected with RDCNN_EINVAL before any GPU work;
+//    grids are rejected with RDCNN_EINVAL before any GPU work.  The second
+//    plane starts at the first one's size rounded up to 256 bytes, as in a
+//    handle's workspace, so both planes keep the array's alignment;
+//  - the update is the paper's: the toroidal boundary (there is no boundary
+//    argument; zero-flux grids need rdcnn_run);
 //  - all calls share the one array, so calls whose GPU work overlaps in time
 //    (different streams, different host threads on the same device) race on
 //    it and corrupt each other: serialise them;
@@ -21,7 +25,10 @@
 //    reads scratch before writing it, so nothing needs clearing;
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress, which may load the module on that device); make
-//    that first call before starting any stream capture on the device.
+//    that first call before starting any stream capture on the device;
+//  - that address is kept for the life of the process: do not use this
+//    entry point after a cudaDeviceReset (or any teardown of the device's
+//    primary context) in the same process, where it would be stale.
 #include <cmath>
 #include <mutex>
 
@@ -78,7 +85,7 @@ int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, i
     if (!u || !v) return set_error(RDCNN_EINVAL, "state pointers must be non-NULL");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     const size_t plane = (size_t)nn * (size_t)nm * elem_size(dtype);
-    if (plane > kStaticScratchBytes / 2)
+    if (plane > kStaticScratchBytes / 2 || plane_stride(plane) + plane > kStaticScratchBytes)
         return set_error(RDCNN_EINVAL,
                          "grid %lld x %lld needs %zu bytes of scratch; the static scratch holds %zu "
                          "(at most %zu cells of this dtype)",
@@ -93,7 +100,7 @@ int rdcnn_run_static(int64_t nn, int64_t nm, const rdcnn_params *p, int dtype, i
     if (sc < 0) return sc;
     cudaStream_t s = (cudaStream_t)stream;
     void *su = scratch;
-    void *sv = (char *)scratch + plane;
+    void *sv = (char *)scratch + plane_stride(plane);
     const bool vec = (nm % vec_width(dtype) == 0) && aligned16(u) && aligned16(v) && aligned16(sv);
     const void *cu = u, *cv = v;
     void *nu = su, *nv = sv;
