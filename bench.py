@@ -518,12 +518,41 @@ def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
     g.set_state(x, x).run(T)
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
+
+    # training-loop form: the forward that produces the loss records a tape (rdcnn_run_record),
+    # the backward reads it (rdcnn_adjoint_tape) instead of sweeping forward again
+    def tape_pass(nck):
+        g.set_state(x, x)
+        tape = g.run_record(T, nck)
+        _, wb = g.tape_bytes(T, nck)
+        wst = torch.empty(wb, dtype=torch.uint8, device="cuda")
+        g.adjoint_tape(T, tape, gu, gv, nck, workspace=wst)  # warm
+        g.set_state(x, x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.run_record(T, nck, tape=tape)
+        torch.cuda.synchronize()
+        t_rec = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        g.adjoint_tape(T, tape, gu, gv, nck, workspace=wst)
+        t_bwd = time.perf_counter() - t0
+        nb = tape.numel()
+        del tape, wst
+        return {"n_checkpoints": nck if nck else int(np.ceil(np.sqrt(T))), "tape_bytes": int(nb),
+                "record_ms": t_rec * 1e3, "backward_ms": t_bwd * 1e3, "record_over_fwd": t_rec / t_fwd,
+                "backward_over_fwd": t_bwd / t_fwd, "fwd_plus_bwd_over_fwd": (t_rec + t_bwd) / t_fwd}
+
+    tape_sqrt = tape_pass(0)
+    tape_all = tape_pass(T)
     g.close()
     return {"grid": [N, N], "T": T, "checkpoints": int(np.ceil(np.sqrt(T))), "adjoint_ms": t_adj * 1e3,
             "plain_fwd_ms": t_fwd * 1e3, "adjoint_over_fwd": t_adj / t_fwd,
             "value": N * N * T / t_adj / 1e9, "unit": "Gcell-updates/s (forward steps differentiated)",
             "all_states": {"checkpoints": 1, "adjoint_ms": t_all * 1e3, "adjoint_over_fwd": t_all / t_fwd,
                            "workspace_bytes": int(all_bytes)},
+            "tape": {"sqrt": tape_sqrt, "all": tape_all,
+                     "note": "backward_ms: rdcnn_adjoint_tape after a recording forward (rdcnn_run_record) "
+                             "of the same T; adjoint_ms above includes its own forward sweep"},
             "gradient_check": adjoint_gradient_check(rd, torch, N=N, T=T, quick=quick)}
 
 
@@ -802,6 +831,11 @@ def followon_summary(line):
         out["adjoint"] = {"ms": a["adjoint_ms"], "plain_fwd_ms": a["plain_fwd_ms"],
                           "adjoint_over_fwd": a["adjoint_over_fwd"],
                           "all_states_over_fwd": a["all_states"]["adjoint_over_fwd"]}
+        if "tape" in a:
+            for key in ("sqrt", "all"):
+                t = a["tape"][key]
+                out["adjoint"][f"tape_{key}"] = {"record_over_fwd": t["record_over_fwd"],
+                                                 "backward_over_fwd": t["backward_over_fwd"]}
         gc = a.get("gradient_check")
         if gc:
             sh, wl = gc["short_horizon"], gc.get("workload_horizon")

@@ -304,7 +304,8 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
  * and the co-state dL/du_T, dL/dv_T of a loss L of the final state, writes
  * dL/du0, dL/dv0 (device planes) and grad[6] = dL/d{Du, Dv, a, b, eps, c}
  * (host array, FP64).  Forward states are rebuilt from n_checkpoints stored
- * states (0 = ceil(sqrt(T))).  All planes are device planes of the handle's
+ * states (0 = ceil(sqrt(T)); n_checkpoints >= T stores every state, T planes
+ * pairs of workspace, and rebuilds nothing).  All planes are device planes of the handle's
  * size and dtype; the bound u/v/workspace of the handle are not touched.
  * The handle's boundary applies (the zero-flux Laplacian, like the periodic
  * one, is symmetric, so the co-state diffuses under the same operator), and
@@ -320,6 +321,46 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0,
                   const void *dLdu_T, const void *dLdv_T, int64_t n_checkpoints,
                   void *dLdu0, void *dLdv0, double grad[6],
                   void *workspace, size_t workspace_bytes);
+
+/* ------------------------------------------------------------------ recorded forward + adjoint */
+
+/* For training loops, where the forward run that produces the loss happens
+ * anyway: rdcnn_run_record records the states the adjoint needs while it
+ * runs, and rdcnn_adjoint_tape then skips rdcnn_adjoint's own forward sweep.
+ * Not in the paper, like the adjoint.
+ *
+ * Tape layout (device memory, caller-owned, 16-byte aligned): slot i
+ * (i = 0 .. nseg - 1) holds the state at step i*S as two planes, u then v,
+ * each padded to a multiple of 256 bytes, where S = ceil(T / n) and
+ * nseg = ceil(T / S) for n = n_checkpoints (0 = ceil(sqrt(T)); n >= T keeps
+ * every state 0 .. T-1, and the adjoint then recomputes nothing).
+ * rdcnn_tape_bytes gives the tape size and the workspace rdcnn_adjoint_tape
+ * needs for that n (both depend on the handle's tune k, as for
+ * rdcnn_adjoint: set the tune first).  FP32 / FP64 handles, NM a multiple of
+ * 4 (F32) or 2 (F64).  Errors: RDCNN_EINVAL. */
+int rdcnn_tape_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpoints, size_t *tape_bytes,
+                     size_t *workspace_bytes);
+
+/* rdcnn_run(h, T, RDCNN_VARIANT_AUTO, 0) that also writes the tape: the bound
+ * state advances by T steps (the same bits as rdcnn_run) and slot i of the
+ * tape receives the state at step i*S of this run (slot 0: the state at the
+ * call).  Uses the bound workspace as scratch; asynchronous on the bound
+ * stream.  The bound buffers and the tape must be 16-byte aligned.
+ * Errors: RDCNN_ESTATE, RDCNN_EINVAL, RDCNN_ESPACE (tape too small),
+ * RDCNN_ECUDA. */
+int rdcnn_run_record(rdcnn_t *h, int64_t T, int64_t n_checkpoints, void *tape, size_t tape_bytes);
+
+/* rdcnn_adjoint with the forward states read from a tape that
+ * rdcnn_run_record wrote for the same T, n_checkpoints, gene, tune and
+ * boundary (the start state is the tape's slot 0, so u0 and v0 are not
+ * passed).  The tape is only read.  Outputs, synchronisation and errors as
+ * for rdcnn_adjoint (RDCNN_ESPACE also for a short tape); the results are
+ * those rdcnn_adjoint returns for that start state and n_checkpoints, bit
+ * for bit.  workspace: at least the *workspace_bytes rdcnn_tape_bytes
+ * reports. */
+int rdcnn_adjoint_tape(rdcnn_t *h, int64_t T, int64_t n_checkpoints, const void *tape, size_t tape_bytes,
+                       const void *dLdu_T, const void *dLdv_T, void *dLdu0, void *dLdv0, double grad[6],
+                       void *workspace, size_t workspace_bytes);
 
 /* ------------------------------------------------------------------ no-allocation run */
 

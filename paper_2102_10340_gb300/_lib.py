@@ -85,6 +85,10 @@ SIGNATURES = [
     ("rdcnn_adjoint_workspace_bytes", c_int, [c_vp, c_i64, c_i64, ctypes.POINTER(c_size)]),
     ("rdcnn_adjoint", c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,
                               ctypes.POINTER(c_double), c_vp, c_size]),
+    ("rdcnn_tape_bytes", c_int, [c_vp, c_i64, c_i64, ctypes.POINTER(c_size), ctypes.POINTER(c_size)]),
+    ("rdcnn_run_record", c_int, [c_vp, c_i64, c_i64, c_vp, c_size]),
+    ("rdcnn_adjoint_tape", c_int, [c_vp, c_i64, c_i64, c_vp, c_size, c_vp, c_vp, c_vp, c_vp,
+                                   ctypes.POINTER(c_double), c_vp, c_size]),
     ("rdcnn_run_static", c_int, [c_i64, c_i64, ctypes.POINTER(Params), c_int, c_int, c_vp, c_vp, c_i64,
                                  c_int, c_vp]),
     ("rdcnn_last_error", ctypes.c_char_p, []),

@@ -133,13 +133,19 @@ cudaError_t forward_all_launch(int reaction, int boundary, int k, int H, const v
     });
 }
 
+// Workspace (and tape) layout of one adjoint call.  Checkpoint slot i holds
+// the state at step i*S.  With S = 1 (n_checkpoints >= T) every state is a
+// checkpoint -- a full tape -- and nothing is rebuilt: the reverse sweep reads
+// the slots directly.  own_ck: the checkpoints live in the workspace
+// (rdcnn_adjoint) rather than in a caller's tape (rdcnn_adjoint_tape).
 struct AdjLayout {
     int64_t S, nseg, nslots, nsets;  // nsets: segment buffer sets (2 when segments can overlap)
+    bool full;
     int ka, H;  // depth of the recompute / reverse launches, halo lanes of the warp map
-    size_t plane, ck_off, seg_off, lam_off, part_off, out_off, total;
+    size_t plane, ck_off, seg_off, lam_off, part_off, out_off, total, tape;
 };
 
-AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck, int tune_k) {
+AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck, int tune_k, bool own_ck) {
     AdjLayout L{};
     L.ka = adj_depth(dtype, tune_k);
     L.H = adj_halo(dtype, L.ka);
@@ -147,12 +153,14 @@ AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck, 
     nck = std::max<int64_t>(1, std::min<int64_t>(nck, std::max<int64_t>(T, 1)));
     L.S = (std::max<int64_t>(T, 1) + nck - 1) / nck;
     L.nseg = (std::max<int64_t>(T, 1) + L.S - 1) / L.S;
-    L.nslots = std::max<int64_t>(L.S, 2);
-    L.nsets = L.nseg > 1 ? 2 : 1;
+    L.full = (L.S == 1 && T > 1);
+    L.nslots = L.full ? 0 : std::max<int64_t>(L.S, 2);
+    L.nsets = L.full ? 0 : (L.nseg > 1 ? 2 : 1);
     L.plane = (((size_t)nn * nm * elem_size(dtype)) + 255) & ~(size_t)255;
     const PipeShape sh = pipe_shape(dtype, nn, nm, L.H);
+    L.tape = (size_t)L.nseg * 2 * L.plane;
     L.ck_off = 0;
-    L.seg_off = L.ck_off + (size_t)L.nseg * 2 * L.plane;
+    L.seg_off = own_ck ? L.tape : 0;
     L.lam_off = L.seg_off + (size_t)L.nsets * L.nslots * 2 * L.plane;
     L.part_off = L.lam_off + 4 * L.plane;
     L.out_off = L.part_off + (((size_t)sh.nwarps * 6 * sizeof(double) + 255) & ~(size_t)255);
@@ -178,13 +186,70 @@ bool adj_streams(rdcnn_t *h) {
     return true;
 }
 
+// Forward from the state in `ck` slot 0 (already written): fill checkpoint
+// slots 1 .. nseg-1 (the state every S steps), with (tu, tv) as scratch
+// planes; with lu_ non-NULL, continue through step T into (lu_, lv_).  The
+// launches of a stretch alternate between the scratch pair and the stretch's
+// destination and end in the destination, so no launch reads the planes it
+// writes.
+// Launch shapes: the temporal kernel at the size's default depth between
+// checkpoints; for a full tape (S = 1) the store-all pipeline, which writes
+// ka consecutive states per launch.  Every variant computes the same bits,
+// so the states are those rdcnn_run produces.
 template <typename T>
-int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary,
-              cudaStream_t s, int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T,
-              const void *dLdv_T, const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
+int record_states(int dtype, int reaction, int boundary, int64_t nn, int64_t nm, const rdcnn_params &p,
+                  cudaStream_t s, int64_t nsteps, const AdjLayout &L, char *ck, void *tu, void *tv, void *lu_,
+                  void *lv_) {
+    auto ck_u = [&](int64_t i) { return (T *)(ck + (size_t)(2 * i) * L.plane); };
+    auto ck_v = [&](int64_t i) { return (T *)(ck + (size_t)(2 * i + 1) * L.plane); };
+    cudaError_t e = cudaSuccess;
+    if (L.full) {
+        const PipeShape sh = pipe_shape(dtype, nn, nm, L.H);
+        for (int64_t q = 0; q + 1 < L.nseg;) {
+            const int kk = (int)std::min<int64_t>(L.ka, L.nseg - 1 - q);
+            StagePlanes<T> pl{};
+            for (int j = 0; j < kk; ++j) { pl.u[j] = ck_u(q + 1 + j); pl.v[j] = ck_v(q + 1 + j); }
+            e = forward_all_launch<T>(reaction, boundary, kk, L.H, ck_u(q), ck_v(q), pl, nn, nm, sh, p, s);
+            if (e != cudaSuccess) return cuda_error(e, "tape recompute");
+            q += kk;
+        }
+    }
+    const int kf = default_k(dtype, nn, nm);
+    auto advance = [&](const void *cu, const void *cv, int64_t len, void *ou, void *ov) -> cudaError_t {
+        const int64_t nl = (len + kf - 1) / kf;
+        for (int64_t j = 0; j < nl; ++j) {
+            const int kk = (int)std::min<int64_t>(kf, len - j * kf);
+            const bool to_dest = ((nl - 1 - j) % 2) == 0;
+            void *nu = to_dest ? ou : tu;
+            void *nv = to_dest ? ov : tv;
+            const cudaError_t le = launch_temporal(dtype, reaction, boundary, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
+            if (le != cudaSuccess) return le;
+            cu = nu; cv = nv;
+        }
+        return cudaSuccess;
+    };
+    if (!L.full) {
+        for (int64_t i = 0; i + 1 < L.nseg && nsteps > 0; ++i) {
+            e = advance(ck_u(i), ck_v(i), L.S, ck_u(i + 1), ck_v(i + 1));
+            if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
+        }
+    }
+    if (lu_) {
+        const int64_t rest = nsteps - (L.nseg - 1) * L.S;
+        if (rest > 0) e = advance(ck_u(L.nseg - 1), ck_v(L.nseg - 1), rest, lu_, lv_);
+        if (e != cudaSuccess) return cuda_error(e, "forward to the final state");
+    }
+    return RDCNN_OK;
+}
+
+// The reverse sweep given the checkpoints in `ck` (slot i = state at step i*S).
+template <typename T>
+int reverse_sweep(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary,
+                  cudaStream_t s, int64_t nsteps, const void *dLdu_T, const void *dLdv_T, const AdjLayout &L,
+                  const char *ck, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
     const size_t bytes = (size_t)nn * nm * sizeof(T);
-    auto ck_u = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i) * L.plane); };
-    auto ck_v = [&](int64_t i) { return (T *)(ws + L.ck_off + (size_t)(2 * i + 1) * L.plane); };
+    auto ck_u = [&](int64_t i) { return (T *)(ck + (size_t)(2 * i) * L.plane); };
+    auto ck_v = [&](int64_t i) { return (T *)(ck + (size_t)(2 * i + 1) * L.plane); };
     int set = 0;  // buffer set of the segment being rebuilt / swept
     auto seg_u = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * (set * L.nslots + i)) * L.plane); };
     auto seg_v = [&](int64_t i) { return (T *)(ws + L.seg_off + (size_t)(2 * (set * L.nslots + i) + 1) * L.plane); };
@@ -200,38 +265,38 @@ int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dty
     double *partial = (double *)(ws + L.part_off);
     double *gout = (double *)(ws + L.out_off);
     const PipeShape sh = pipe_shape(dtype, nn, nm, L.H);
-    const int kf = default_k(dtype, nn, nm);  // depth of the checkpoint sweep
-    const int ka = L.ka;                      // depth of recompute / reverse launches
+    const int ka = L.ka;  // depth of recompute / reverse launches
 
     cudaError_t e = cudaMemcpyAsync(lam_u[0], dLdu_T, bytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam_v[0], dLdv_T, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_u(0), u0, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ck_v(0), v0, bytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, (size_t)sh.nwarps * 6 * sizeof(double), s);
     if (e != cudaSuccess) return cuda_error(e, "adjoint setup copies");
-
-    // forward sweep: checkpoint i = state at step i*S
-    for (int64_t i = 0; i + 1 < L.nseg && nsteps > 0; ++i) {
-        const int64_t len = L.S;
-        const int64_t nl = (len + kf - 1) / kf;
-        const void *cu = ck_u(i), *cv = ck_v(i);
-        for (int64_t j = 0; j < nl; ++j) {
-            const int kk = (int)std::min<int64_t>(kf, len - j * kf);
-            void *nu = (j == nl - 1) ? (void *)ck_u(i + 1) : (void *)seg_u(j % 2);
-            void *nv = (j == nl - 1) ? (void *)ck_v(i + 1) : (void *)seg_v(j % 2);
-            e = launch_temporal(dtype, reaction, boundary, kk, cu, cv, nu, nv, nn, nm, p, 0, s);
-            if (e != cudaSuccess) return cuda_error(e, "adjoint forward sweep");
-            cu = nu; cv = nv;
-        }
-    }
     if (overlap) {  // the rebuilds read the checkpoints
         e = cudaEventRecord(h->adj_ev[0], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, h->adj_ev[0], 0);
         if (e != cudaSuccess) return fail(e, "adjoint stream order");
     }
-    // segments last to first: rebuild the states, then sweep the co-state back
     int cur = 0;
-    for (int64_t sg = L.nseg - 1; sg >= 0 && nsteps > 0; --sg) {
+    auto sweep_back = [&](int64_t len, auto state_u, auto state_v) -> cudaError_t {
+        for (int64_t qh = len; qh > 0;) {
+            const int kk = (int)std::min<int64_t>(ka, qh);
+            StagePlanes<T> st{};
+            for (int j = 0; j < kk; ++j) { st.u[j] = state_u(qh - 1 - j); st.v[j] = state_v(qh - 1 - j); }
+            const cudaError_t le = reverse_launch<T>(reaction, boundary, kk, L.H, lam_u[cur], lam_v[cur], lam_u[cur ^ 1],
+                                                     lam_v[cur ^ 1], st, partial, nn, nm, sh, p, s);
+            if (le != cudaSuccess) return le;
+            cur ^= 1;
+            qh -= kk;
+        }
+        return cudaSuccess;
+    };
+    if (L.full) {
+        // every state is a checkpoint: one sweep over the whole horizon, nothing rebuilt
+        if (nsteps > 0) e = sweep_back(nsteps, ck_u, ck_v);
+        if (e != cudaSuccess) return fail(e, "adjoint reverse step");
+    }
+    // segments last to first: rebuild the states, then sweep the co-state back
+    for (int64_t sg = L.nseg - 1; !L.full && sg >= 0 && nsteps > 0; --sg) {
         const int64_t len = std::min<int64_t>(L.S, nsteps - sg * L.S);
         set = overlap ? (int)((L.nseg - 1 - sg) & 1) : 0;
         auto state_u = [&](int64_t q) { return q == 0 ? ck_u(sg) : seg_u(q); };
@@ -253,16 +318,8 @@ int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dty
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->adj_ev[1 + set], 0);
             if (e != cudaSuccess) return fail(e, "adjoint stream order");
         }
-        for (int64_t qh = len; qh > 0;) {
-            const int kk = (int)std::min<int64_t>(ka, qh);
-            StagePlanes<T> st{};
-            for (int j = 0; j < kk; ++j) { st.u[j] = state_u(qh - 1 - j); st.v[j] = state_v(qh - 1 - j); }
-            e = reverse_launch<T>(reaction, boundary, kk, L.H, lam_u[cur], lam_v[cur], lam_u[cur ^ 1], lam_v[cur ^ 1], st,
-                                  partial, nn, nm, sh, p, s);
-            if (e != cudaSuccess) return fail(e, "adjoint reverse step");
-            cur ^= 1;
-            qh -= kk;
-        }
+        e = sweep_back(len, state_u, state_v);
+        if (e != cudaSuccess) return fail(e, "adjoint reverse step");
         if (overlap) {
             e = cudaEventRecord(h->adj_ev[3 + set], s);
             if (e != cudaSuccess) return fail(e, "adjoint stream order");
@@ -282,6 +339,35 @@ int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dty
     return RDCNN_OK;
 }
 
+// rdcnn_adjoint: checkpoints recorded into the workspace, then the reverse sweep.
+template <typename T>
+int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dtype, int reaction, int boundary,
+              cudaStream_t s, int64_t nsteps, const void *u0, const void *v0, const void *dLdu_T,
+              const void *dLdv_T, const AdjLayout &L, char *ws, void *dLdu0, void *dLdv0, double grad[6]) {
+    const size_t bytes = (size_t)nn * nm * sizeof(T);
+    char *ck = ws + L.ck_off;
+    cudaError_t e = cudaMemcpyAsync(ck, u0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck + L.plane, v0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint setup copies");
+    // a co-state plane pair serves as the sweep's scratch until the reverse sweep starts
+    char *lam = ws + L.lam_off;
+    const int rc = record_states<T>(dtype, reaction, boundary, nn, nm, p, s, nsteps, L, ck, lam, lam + L.plane,
+                                    nullptr, nullptr);
+    if (rc < 0) return rc;
+    return reverse_sweep<T>(h, nn, nm, p, dtype, reaction, boundary, s, nsteps, dLdu_T, dLdv_T, L, ck, ws, dLdu0,
+                            dLdv0, grad);
+}
+
+// Shared checks of the adjoint entry points.
+int adjoint_checks(const rdcnn_t *h, int64_t T, int dtype, int64_t nm) {
+    (void)h;
+    if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
+    if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
+    const int V = vec_width(dtype);
+    if (nm % V != 0) return set_error(RDCNN_EINVAL, "adjoint needs NM %% %d == 0", V);
+    return RDCNN_OK;
+}
+
 }  // namespace
 
 }  // namespace rdk
@@ -298,7 +384,7 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
     if (rc < 0) return rc;
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
-    *bytes = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k).total;
+    *bytes = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k, true).total;
     return RDCNN_OK;
 }
 
@@ -308,16 +394,14 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
-    if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
-    if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
+    rc = adjoint_checks(h, T, dtype, nm);
+    if (rc < 0) return rc;
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
         return set_error(RDCNN_EINVAL, "NULL argument");
-    const int V = vec_width(dtype);
-    if (nm % V != 0) return set_error(RDCNN_EINVAL, "adjoint needs NM %% %d == 0", V);
     const void *ptrs[7] = {u0, v0, dLdu_T, dLdv_T, dLdu0, dLdv0, workspace};
     for (const void *q : ptrs)
         if (!aligned16(q)) return set_error(RDCNN_EINVAL, "adjoint buffers must be 16-byte aligned");
-    const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k);
+    const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k, true);
     if (workspace_bytes < L.total)
         return set_error(RDCNN_ESPACE, "adjoint workspace has %zu bytes, need %zu", workspace_bytes, L.total);
     if (dtype == RDCNN_F64)
@@ -325,6 +409,70 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
                                  (char *)workspace, dLdu0, dLdv0, grad);
     return adjoint_t<float>(h, nn, nm, p, dtype, reaction, boundary, s, T, u0, v0, dLdu_T, dLdv_T, L,
                             (char *)workspace, dLdu0, dLdv0, grad);
+}
+
+int rdcnn_tape_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpoints, size_t *tape_bytes,
+                     size_t *workspace_bytes) {
+    int64_t nn, nm; rdcnn_params p; int dtype, reaction; cudaStream_t s;
+    if (!tape_bytes || !workspace_bytes) return set_error(RDCNN_EINVAL, "NULL output");
+    const int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s);
+    if (rc < 0) return rc;
+    if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
+    if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
+    const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k, false);
+    *tape_bytes = L.tape;
+    *workspace_bytes = L.total;
+    return RDCNN_OK;
+}
+
+int rdcnn_run_record(rdcnn_t *h, int64_t T, int64_t n_checkpoints, void *tape, size_t tape_bytes) {
+    int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
+    int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
+    if (rc < 0) return rc;
+    if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
+    rc = adjoint_checks(h, T, dtype, nm);
+    if (rc < 0) return rc;
+    if (!tape) return set_error(RDCNN_EINVAL, "tape is NULL");
+    if (!aligned16(tape) || !aligned16(h->u) || !aligned16(h->v) || !aligned16(h->ws))
+        return set_error(RDCNN_EINVAL, "the tape and the bound buffers must be 16-byte aligned");
+    const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k, false);
+    if (tape_bytes < L.tape) return set_error(RDCNN_ESPACE, "tape has %zu bytes, need %zu", tape_bytes, L.tape);
+    const size_t bytes = (size_t)nn * nm * elem_size(dtype);
+    char *ck = (char *)tape;
+    cudaError_t e = cudaMemcpyAsync(ck, h->u, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck + L.plane, h->v, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "tape slot 0");
+    if (T == 0) return RDCNN_OK;
+    // scratch: the bound ping-pong planes (second one at the rounded stride)
+    char *ws = (char *)h->ws;
+    void *su = ws, *sv = ws + plane_stride(bytes);
+    if (dtype == RDCNN_F64)
+        return record_states<double>(dtype, reaction, boundary, nn, nm, p, s, T, L, ck, su, sv, h->u, h->v);
+    return record_states<float>(dtype, reaction, boundary, nn, nm, p, s, T, L, ck, su, sv, h->u, h->v);
+}
+
+int rdcnn_adjoint_tape(rdcnn_t *h, int64_t T, int64_t n_checkpoints, const void *tape, size_t tape_bytes,
+                       const void *dLdu_T, const void *dLdv_T, void *dLdu0, void *dLdv0, double grad[6],
+                       void *workspace, size_t workspace_bytes) {
+    int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
+    int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
+    if (rc < 0) return rc;
+    rc = adjoint_checks(h, T, dtype, nm);
+    if (rc < 0) return rc;
+    if (!tape || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
+        return set_error(RDCNN_EINVAL, "NULL argument");
+    const void *ptrs[6] = {tape, dLdu_T, dLdv_T, dLdu0, dLdv0, workspace};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return set_error(RDCNN_EINVAL, "adjoint buffers must be 16-byte aligned");
+    const AdjLayout L = adj_layout(dtype, nn, nm, T, n_checkpoints, h->tune_k, false);
+    if (tape_bytes < L.tape) return set_error(RDCNN_ESPACE, "tape has %zu bytes, need %zu", tape_bytes, L.tape);
+    if (workspace_bytes < L.total)
+        return set_error(RDCNN_ESPACE, "adjoint workspace has %zu bytes, need %zu", workspace_bytes, L.total);
+    if (dtype == RDCNN_F64)
+        return reverse_sweep<double>(h, nn, nm, p, dtype, reaction, boundary, s, T, dLdu_T, dLdv_T, L,
+                                     (const char *)tape, (char *)workspace, dLdu0, dLdv0, grad);
+    return reverse_sweep<float>(h, nn, nm, p, dtype, reaction, boundary, s, T, dLdu_T, dLdv_T, L, (const char *)tape,
+                                (char *)workspace, dLdu0, dLdv0, grad);
 }
 
 }  // extern "C"

@@ -259,6 +259,42 @@ class Grid:
         return du0, dv0, dict(zip(GRAD_NAMES, list(grad)))
 
 
+    def tape_bytes(self, T: int, n_checkpoints: int = 0):
+        """(tape bytes, workspace bytes) of a recorded run of T steps (see run_record)."""
+        tb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        L.check(self.lib.rdcnn_tape_bytes(self.h, int(T), int(n_checkpoints), ctypes.byref(tb), ctypes.byref(wb)))
+        return tb.value, wb.value
+
+    def run_record(self, T: int, n_checkpoints: int = 0, tape=None):
+        """run(T) that also records the states a later adjoint_tape needs; returns the tape
+        (a uint8 device tensor; n_checkpoints = 0: ceil(sqrt(T)) stored states, >= T: all)."""
+        nbytes, _ = self.tape_bytes(T, n_checkpoints)
+        if tape is None or tape.numel() < nbytes:
+            tape = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+        self._bind()
+        L.check(self.lib.rdcnn_run_record(self.h, int(T), int(n_checkpoints), _vp(tape), tape.numel()))
+        return tape
+
+    def adjoint_tape(self, T: int, tape, gu, gv, n_checkpoints: int = 0, workspace=None):
+        """adjoint() from a tape written by run_record(T, n_checkpoints) (same start state)."""
+        planes = []
+        for t, name in ((gu, "dL/du_T"), (gv, "dL/dv_T")):
+            t = torch.as_tensor(t, device=self.device).to(self.dtype).contiguous()
+            _plane_check(t, self.nn, self.nm, self.dtype, name)
+            planes.append(t)
+        gu, gv = planes
+        du0 = torch.empty_like(gu)
+        dv0 = torch.empty_like(gv)
+        _, nbytes = self.tape_bytes(T, n_checkpoints)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = (ctypes.c_double * 6)()
+        self._bind()
+        L.check(self.lib.rdcnn_adjoint_tape(self.h, int(T), int(n_checkpoints), _vp(tape), tape.numel(), _vp(gu),
+                                            _vp(gv), _vp(du0), _vp(dv0), grad, _vp(workspace), workspace.numel()))
+        return du0, dv0, dict(zip(GRAD_NAMES, list(grad)))
+
+
 def run(u: torch.Tensor, v: torch.Tensor, params: dict | None, T: int, variant: str = "auto",
         k: int = 0, reaction: str = "fhn", boundary: str = "periodic"):
     """Advance (u, v) in place by T steps of Eq. 1 (scratch allocated by torch)."""
@@ -402,8 +438,11 @@ def grid_summary(u: torch.Tensor, v: torch.Tensor, threshold: float = 0.05):
 class RDCNNFunction(torch.autograd.Function):
     """(u0, v0, theta) -> (u_T, v_T), theta = [Du, Dv, a, b, eps, c] (a float64 tensor).
 
-    Forward runs T steps of Eq. 1; backward runs the reverse-time adjoint
-    (``rdcnn_adjoint``, sqrt(T) checkpoints) and returns dL/du0, dL/dv0, dL/dtheta.
+    Forward runs T steps of Eq. 1 and records n_checkpoints states on the way
+    (``rdcnn_run_record``; 0 = ceil(sqrt(T)), >= T = every state); backward runs the
+    reverse-time adjoint from that tape (``rdcnn_adjoint_tape``) and returns dL/du0, dL/dv0,
+    dL/dtheta.  float64 planes run the FP64 kernels throughout (forward, tape and adjoint),
+    the choice for initial-state gradients that must match finite differences closely.
     ``boundary``: "periodic" (the paper's torus) or "zeroflux"; ``reaction``: "fhn", "none" or
     "cenn" (then u0 is the cell state, v0 the offset plane, and theta's Du / c entries the
     neighbour / self feedback weights).
@@ -418,7 +457,7 @@ class RDCNNFunction(torch.autograd.Function):
         g = Grid(u0.shape[0], u0.shape[1], params, dtype=u0.dtype, device=u0.device, boundary=boundary,
                  reaction=reaction)
         g.set_state(u0.detach(), v0.detach())
-        g.run(int(T))
+        ctx.tape = g.run_record(int(T), int(n_checkpoints))
         uT, vT = g.state()
         ctx.save_for_backward(u0.detach(), v0.detach())
         ctx.grid = g
@@ -436,6 +475,6 @@ class RDCNNFunction(torch.autograd.Function):
             gu = torch.zeros_like(u0)
         if gv is None:
             gv = torch.zeros_like(v0)
-        du0, dv0, gp = g.adjoint(ctx.T, u0, v0, gu.contiguous(), gv.contiguous(), ctx.nck)
+        du0, dv0, gp = g.adjoint_tape(ctx.T, ctx.tape, gu.contiguous(), gv.contiguous(), ctx.nck)
         gtheta = torch.tensor([gp[k] for k in GRAD_NAMES], dtype=ctx.theta_dtype, device=ctx.theta_device)
         return du0, dv0, gtheta, None, None, None, None, None

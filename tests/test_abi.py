@@ -180,6 +180,38 @@ def test_adjoint_validation(lib, L):
     lib.rdcnn_destroy(h)
 
 
+def test_tape_layout_and_validation(lib, L):
+    """Host-side rules of the recorded-forward entry points (no GPU work happens)."""
+    rc, h = _create(lib, L, nn=4, nm=8)  # FP32: one plane is 128 bytes, padded to 256
+    tb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.rdcnn_tape_bytes(h, 100, 0, ctypes.byref(tb), ctypes.byref(wb)) == L.OK
+    assert tb.value == 10 * 2 * 256  # ceil(sqrt(100)) = 10 slots of (u, v)
+    assert lib.rdcnn_tape_bytes(h, 100, 7, ctypes.byref(tb), ctypes.byref(wb)) == L.OK
+    assert tb.value == 7 * 2 * 256  # S = ceil(100 / 7) = 15, ceil(100 / 15) = 7 slots
+    assert lib.rdcnn_tape_bytes(h, 100, 100, ctypes.byref(tb), ctypes.byref(wb)) == L.OK
+    assert tb.value == 100 * 2 * 256  # every state 0 .. 99
+    full_ws = wb.value
+    assert lib.rdcnn_tape_bytes(h, 100, 0, ctypes.byref(tb), ctypes.byref(wb)) == L.OK
+    assert full_ws < wb.value  # a full tape needs no segment buffers
+    a = ctypes.c_size_t()
+    assert lib.rdcnn_adjoint_workspace_bytes(h, 100, 0, ctypes.byref(a)) == L.OK
+    assert a.value == wb.value + tb.value  # rdcnn_adjoint keeps its checkpoints in the workspace
+    assert lib.rdcnn_tape_bytes(h, -1, 0, ctypes.byref(tb), ctypes.byref(wb)) == L.EINVAL
+    assert lib.rdcnn_tape_bytes(h, 10, 0, None, ctypes.byref(wb)) == L.EINVAL
+    # recording needs a bound handle; the tape must be present, aligned and large enough
+    assert lib.rdcnn_run_record(h, 10, 0, 4096, 1 << 20) == L.ESTATE
+    g = (ctypes.c_double * 6)()
+    assert lib.rdcnn_adjoint_tape(h, 10, 0, None, 0, 256, 512, 768, 1024, g, 4096, 1 << 20) == L.EINVAL
+    assert lib.rdcnn_adjoint_tape(h, 10, 0, 4100, 1 << 20, 256, 512, 768, 1024, g, 4096, 1 << 20) == L.EINVAL
+    assert lib.rdcnn_adjoint_tape(h, 10, 0, 8192, 16, 256, 512, 768, 1024, g, 4096, 1 << 20) == L.ESPACE
+    assert lib.rdcnn_adjoint_tape(h, 10, 0, 8192, 1 << 20, 256, 512, 768, 1024, g, 4096, 16) == L.ESPACE
+    assert lib.rdcnn_adjoint_tape(h, -3, 0, 8192, 1 << 20, 256, 512, 768, 1024, g, 4096, 1 << 20) == L.EINVAL
+    lib.rdcnn_destroy(h)
+    rc, h = _create(lib, L, nn=4, nm=8, dtype=L.BF16)
+    assert lib.rdcnn_tape_bytes(h, 10, 0, ctypes.byref(tb), ctypes.byref(wb)) == L.EINVAL
+    lib.rdcnn_destroy(h)
+
+
 def test_version_and_counter(lib):
     assert b"rdcnn" in lib.rdcnn_version()
     assert lib.rdcnn_launch_count() >= 0

@@ -324,3 +324,96 @@ def test_adjoint_depths_match_oracle(rd, oracle_mod, dtype, k, model):
     assert normwise(du.double().cpu().numpy(), ou) <= tol and normwise(dv.double().cpu().numpy(), ov) <= tol
     got = np.array([gp[n] for n in NAMES])
     np.testing.assert_allclose(got, og, rtol=gtol, atol=gtol * np.linalg.norm(og))
+
+
+# ---------------------------------------------------------------------------- recorded forward (tape)
+
+TAPE_MODELS = [("fhn", "periodic"), ("fhn", "zeroflux"), ("cenn", "periodic")]
+
+
+def _tape_grid(rd, reaction, boundary, dtype, nn=40, nm=64):
+    gene = CENN_ADJ if reaction == "cenn" else inp.default_params(Du=0.12, Dv=0.3)
+    return rd.Grid(nn, nm, gene, dtype=dtype, reaction=reaction, boundary=boundary), gene
+
+
+@pytest.mark.parametrize("dtype", [F32, F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("nck", [0, 4, 31], ids=["sqrtT", "nck4", "all"])
+def test_run_record_is_run_and_tape_holds_the_states(rd, dtype, nck):
+    """rdcnn_run_record leaves the bits rdcnn_run leaves, and tape slot i holds the state at
+    step i*S of that run (S = ceil(T / n)); n >= T keeps every state."""
+    nn, nm, T = 40, 64, 31
+    x = inp.uniform_field(51, nn, nm)
+    y = inp.uniform_field(52, nn, nm)
+    if dtype == F32:
+        x, y = f32(x), f32(y)
+    g, gene = _tape_grid(rd, "fhn", "periodic", dtype, nn, nm)
+    g.set_state(_dev(x, dtype), _dev(y, dtype))
+    tape = g.run_record(T, nck)
+    torch.cuda.synchronize()
+    n = int(np.ceil(np.sqrt(T))) if nck == 0 else min(nck, T)
+    S = -(-T // n)
+    nseg = -(-T // S)
+    esz = 4 if dtype == F32 else 8
+    plane = -(-(nn * nm * esz) // 256) * 256
+    assert tape.numel() >= nseg * 2 * plane
+    ref_u, ref_v = gpu_run(rd, x, y, gene, T, dtype)
+    assert np.array_equal(g.u.double().cpu().numpy(), ref_u) and np.array_equal(g.v.double().cpu().numpy(), ref_v)
+    raw = tape.view(torch.uint8)
+    for i in sorted({0, 1, nseg // 2, nseg - 1}):
+        su = raw[2 * i * plane:2 * i * plane + nn * nm * esz].view(dtype).reshape(nn, nm)
+        sv = raw[(2 * i + 1) * plane:(2 * i + 1) * plane + nn * nm * esz].view(dtype).reshape(nn, nm)
+        eu, ev = gpu_run(rd, x, y, gene, i * S, dtype)
+        assert np.array_equal(su.double().cpu().numpy(), eu) and np.array_equal(sv.double().cpu().numpy(), ev), i
+
+
+@pytest.mark.parametrize("dtype", [F32, F64], ids=["f32", "f64"])
+@pytest.mark.parametrize("nck", [0, 5, 27], ids=["sqrtT", "nck5", "all"])
+@pytest.mark.parametrize("model", TAPE_MODELS, ids=["fhn-torus", "fhn-zeroflux", "cenn-torus"])
+def test_adjoint_tape_equals_adjoint(rd, oracle_mod, dtype, nck, model):
+    """The adjoint from a recorded tape gives rdcnn_adjoint's bits (same checkpoints, same
+    launch sequence of the reverse sweep), and the oracle's adjoint within the parity bar."""
+    reaction, boundary = model
+    nn, nm, T = 40, 64, 27
+    scale = 1.7 if reaction == "cenn" else 1.0
+    x = scale * inp.uniform_field(61, nn, nm)
+    y = inp.uniform_field(62, nn, nm)
+    wu = inp.uniform_field(63, nn, nm) / (nn * nm)
+    wv = inp.uniform_field(64, nn, nm) / (nn * nm)
+    if dtype == F32:
+        x, y, wu, wv = f32(x), f32(y), f32(wu), f32(wv)
+    g, gene = _tape_grid(rd, reaction, boundary, dtype, nn, nm)
+    du, dv, gp = g.adjoint(T, _dev(x, dtype), _dev(y, dtype), _dev(wu, dtype), _dev(wv, dtype), nck)
+    g.set_state(_dev(x, dtype), _dev(y, dtype))
+    tape = g.run_record(T, nck)
+    tu, tv, tp = g.adjoint_tape(T, tape, _dev(wu, dtype), _dev(wv, dtype), nck)
+    torch.cuda.synchronize()
+    assert torch.equal(du, tu) and torch.equal(dv, tv)
+    assert all(gp[k] == tp[k] for k in NAMES), (gp, tp)
+    rx = oracle_mod.CENN if reaction == "cenn" else oracle_mod.FHN
+    bc = oracle_mod.ZEROFLUX if boundary == "zeroflux" else oracle_mod.PERIODIC
+    ou, ov, og = oracle_mod.adjoint(x, y, gene, T, wu, wv, n_checkpoints=nck, reaction=rx, boundary=bc)
+    tol, gtol = (1e-10, 1e-9) if dtype == F64 else (1e-5, 1e-5)
+    assert normwise(tu.double().cpu().numpy(), ou) <= tol and normwise(tv.double().cpu().numpy(), ov) <= tol
+    got = np.array([tp[n] for n in NAMES])
+    np.testing.assert_allclose(got, og, rtol=gtol, atol=gtol * np.linalg.norm(og))
+
+
+def test_adjoint_tape_full_size_f32(rd, oracle_mod):
+    """The benchmark's adjoint workload (512^2, T = 2000) from a full tape (every state kept,
+    nothing rebuilt) against the sqrt(T)-checkpoint adjoint: the same co-state bits."""
+    N, T = 512, 2000
+    p = inp.default_params()
+    x = _dev(f32(inp.uniform_field(0, N, N)), F32)
+    target = _dev(inp.checkerboard(0, N, N), F32)
+    g = rd.Grid(N, N, p, dtype=F32)
+    g.set_state(x, x)
+    tape = g.run_record(T, T)
+    gu = (2.0 * (g.u - target) / g.u.numel()).contiguous()
+    du, dv, gp = g.adjoint_tape(T, tape, gu, torch.zeros_like(gu), T)
+    del tape
+    ru, rv, rp = g.adjoint(T, x, x, gu, torch.zeros_like(gu))
+    torch.cuda.synchronize()
+    assert torch.equal(du, ru) and torch.equal(dv, rv)
+    a = np.array([gp[k] for k in NAMES])
+    b = np.array([rp[k] for k in NAMES])
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
