@@ -136,7 +136,8 @@ int rdcnn_set_params(rdcnn_t *h, const rdcnn_params *p);
 /* Set the handle's launch shape (see rdcnn_tune); NULL restores defaults.
  * rdcnn_run uses tune->k when its own k argument is 0, and tune->rows for
  * the rows per warp of every vectorised variant.  rdcnn_adjoint uses tune->k
- * (capped at 8 for F32, 4 for F64; default 4 / 2) as the depth of its
+ * (capped at 8 for F32, 4 for F64; default 4 / 2, and 5 for F32 when every
+ * state is stored) as the depth of its
  * recompute and reverse launches, and sizes its workspace for it: set the
  * tune before rdcnn_adjoint_workspace_bytes.  Errors: RDCNN_EINVAL. */
 int rdcnn_set_tune(rdcnn_t *h, const rdcnn_tune *tune);

@@ -77,11 +77,15 @@ k_reduce_partials(const double *__restrict__ partial, int nwarps, double dt, dou
 
 // Depth of the recompute / reverse launches (handle tune k, else these), and
 // the halo lanes of the call's warp map: one lane while k <= V, else two.
+// Default FP32 depth: 4, and 5 when every state is stored (no rebuild runs
+// beside the reverse sweep; 512^2, T = 2000, 3-row strips: k = 3 / 4 / 5 / 6
+// gave 6.3 / 6.2 / 5.5 / 6.0 ms for the full-tape sweep, 7.8 / 7.8 / 7.8 / 9.5
+// ms with sqrt(T) checkpoints).
 constexpr int kMaxAdjK32 = 8, kMaxAdjK64 = 4;
-inline int adj_depth(int dtype, int tune_k) {
+inline int adj_depth(int dtype, int tune_k, bool full) {
     const int cap = dtype == RDCNN_F64 ? kMaxAdjK64 : kMaxAdjK32;
     if (tune_k > 0) return std::min(tune_k, cap);
-    return dtype == RDCNN_F64 ? 2 : 4;
+    return dtype == RDCNN_F64 ? 2 : (full ? 5 : 4);
 }
 inline int adj_halo(int dtype, int k) { return k <= vec_width(dtype) ? 1 : 2; }
 
@@ -91,9 +95,11 @@ PipeShape pipe_shape(int dtype, int64_t nn, int64_t nm, int H) {
     const int outw = (32 - 2 * H) * V;
     PipeShape s;
     const int64_t cells = nn * nm;
-    // strip length by size class; 512^2 measured 2 / 4 / 8 / 16 rows = 19.6 / 16.4 / 17.5 /
-    // 22.6 ms for the T = 2000 adjoint (short strips fill more SMs, long ones waste less halo)
-    s.rows = cells < (int64_t(1) << 19) ? 4 : cells < (int64_t(1) << 22) ? 16 : 64;
+    // strip length by size class (short strips fill more SMs, long ones waste less halo).
+    // 512^2, T = 2000, FP32 (ms; own checkpoints / sqrt(T) tape / full tape, k = 4):
+    // 1 row 15.6 / 13.0 / 11.9, 2 rows 10.8 / 8.2 / 7.2, 3 rows 10.4 / 7.8 / 6.2,
+    // 4 rows 11.0 / 8.3 / 6.7, 6 rows 10.7 / 8.1 / 6.5, 8 rows 11.4 / 8.7 / 7.4
+    s.rows = cells < (int64_t(1) << 17) ? 4 : cells < (int64_t(1) << 19) ? 3 : cells < (int64_t(1) << 22) ? 16 : 64;
     s.bands = (int)((nm + outw - 1) / outw);
     s.strips = (int)((nn + s.rows - 1) / s.rows);
     s.nwarps = s.bands * s.strips;
@@ -147,13 +153,13 @@ struct AdjLayout {
 
 AdjLayout adj_layout(int dtype, int64_t nn, int64_t nm, int64_t T, int64_t nck, int tune_k, bool own_ck) {
     AdjLayout L{};
-    L.ka = adj_depth(dtype, tune_k);
-    L.H = adj_halo(dtype, L.ka);
     if (nck <= 0) nck = (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(T, 1)));
     nck = std::max<int64_t>(1, std::min<int64_t>(nck, std::max<int64_t>(T, 1)));
     L.S = (std::max<int64_t>(T, 1) + nck - 1) / nck;
     L.nseg = (std::max<int64_t>(T, 1) + L.S - 1) / L.S;
     L.full = (L.S == 1 && T > 1);
+    L.ka = adj_depth(dtype, tune_k, L.full);
+    L.H = adj_halo(dtype, L.ka);
     L.nslots = L.full ? 0 : std::max<int64_t>(L.S, 2);
     L.nsets = L.full ? 0 : (L.nseg > 1 ? 2 : 1);
     L.plane = (((size_t)nn * nm * elem_size(dtype)) + 255) & ~(size_t)255;
