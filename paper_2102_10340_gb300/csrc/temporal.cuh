@@ -28,7 +28,13 @@
 
 namespace rdk {
 
-constexpr int kTemporalWarps = 4;  // warps per block of every kernel built on temporal_strip
+// Warps per block of every kernel built on temporal_strip.  One: the same
+// resident warps per SM issue faster as one-warp blocks (K = 8 at 4096^2:
+// 1436 against 1278 Gcell-updates/s with four-warp blocks and 1270 with
+// two; ncu shows the dispatch stalls per issued instruction falling from
+// 0.44 to 0.18 and issue-active rising from 63 % to 72 % at the same 8
+// warps per SM and the same instructions).
+constexpr int kTemporalWarps = 1;
 // Input rows staged per warp (prefetch distance kRing - 1 = 2 beats, about
 // 1.5 us of the K = 8 pipeline, above the HBM latency).  Three slots match
 // the 3-beat window rotation, so a beat's slots are compile-time constants.
