@@ -389,9 +389,11 @@ def measure_image(rd, torch, N=1024, T=10000, quick=False):
             "note": "state + ping-pong = 16 MiB, L2-resident (126 MiB L2)"}
 
 
-def measure_batched(rd, torch, T=5000, quick=False, tune=None):
+def measure_batched(rd, torch, T=5000, quick=False, tune=None, full_sweep=False):
+    """Batched sweep: the 256-instance workload (or its first 32 instances with quick) advanced T
+    steps by rdcnn_batch_run, against one instance at a time through the single-grid path."""
     specs = inp.sweep_instances(0)
-    if quick:
+    if quick and not full_sweep:
         specs = specs[:32]
         T = 500
     b = rd.Batch(specs, dtype=torch.float32)
@@ -463,7 +465,9 @@ def measure_search(torch, N=256, T=2000, quick=False):
 
 def measure_snapshots(rd, grid, x_dev, torch, T=2000, every=200):
     """Snapshot capture (the paper's A_show / B_show, every `every` steps to pinned host
-    memory) against the same run without snapshots, on the headline grid."""
+    memory) against the same run without snapshots, on the headline grid, with the paper's
+    loop structure (one single-step launch per step)."""
+    grid.set_tune(k=1, rows=0)
     grid.init(x_dev, 1.0).run(T)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -479,7 +483,7 @@ def measure_snapshots(rd, grid, x_dev, torch, T=2000, every=200):
     t_snap = time.perf_counter() - t0
     n = T // every + 1
     nbytes = int(2 * n * us[0].numel() * us.element_size())
-    return {"T": T, "every": every, "snapshots": n, "bytes_to_host": nbytes,
+    return {"T": T, "every": every, "snapshots": n, "bytes_to_host": nbytes, "kernel": "single step (k = 1)",
             "ms": t_snap * 1e3, "plain_ms": t_plain * 1e3, "overhead": t_snap / t_plain - 1.0,
             "host_gbs": nbytes / t_snap / 1e9}
 
@@ -862,8 +866,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="use --variant/--k/--rows instead of autotuning (with --leg batched: --k/--rows)")
-    ap.add_argument("--leg", choices=("batched", "adjoint", "search", "models", "storage", "image"), default=None,
-                    help="run only this follow-on measurement (small, for profiling) and print it")
+    ap.add_argument("--leg", choices=("batched", "batched_full", "adjoint", "search", "models", "storage", "image"),
+                    default=None,
+                    help="run only this follow-on measurement (small, for profiling) and print it; "
+                         "batched_full: all 256 sweep instances for --T steps")
     ap.add_argument("--variant", default="temporal",
                     choices=("temporal", "temporal2", "temporal_wide", "step1", "generic"))
     ap.add_argument("--k", type=int, default=8)
@@ -880,6 +886,7 @@ def main(argv=None):
 
         btune = {"k": args.k, "rows": args.rows} if args.no_tune else None
         fn = {"batched": lambda: measure_batched(rd, torch, quick=True, tune=btune),
+              "batched_full": lambda: measure_batched(rd, torch, T=args.T, quick=True, tune=btune, full_sweep=True),
               "adjoint": lambda: measure_adjoint(rd, torch, quick=True),
               "search": lambda: measure_search(torch, quick=True),
               "models": lambda: measure_models(rd, torch),
