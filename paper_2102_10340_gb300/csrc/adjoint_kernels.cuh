@@ -159,6 +159,7 @@ struct ReversePolicy {
             store_vec<T>(lvn + off, out.v);
         }
     }
+    __device__ __forceinline__ void finish_main(int q, const Slice<T> &out) { finish(q, out); }
     __device__ __forceinline__ void flush(double *__restrict__ slot) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) rg[q] = warp_sum_t(rg[q]);

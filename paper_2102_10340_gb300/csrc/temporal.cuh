@@ -162,6 +162,13 @@ template <int BC> struct RowWalk {
 //        stage s maps rows q-1 (A), q (B), q+1 (C) of its input to row q of
 //        its output (q = input-row index within the strip, see temporal_strip)
 //   P::finish(q, out)                    the row q leaving the last stage
+//   P::finish_main(q, out)               the same for a beat of the main loop,
+//                                        where q >= K holds: the owned row
+//                                        check may be dropped
+//
+// CHECK = false: a beat of the main loop's whole triplets (m + 2 < total),
+// which needs neither the end-of-strip test nor the last-copy test (measured
+// at K = 8, 4096^2: 1427 -> 1448 Gcell-updates/s).
 //
 // ACTIVE < K (the first 2K beats of a strip with a policy that allows it):
 // only stages s < ACTIVE compute; stage ACTIVE just keeps its input row for
@@ -169,17 +176,17 @@ template <int BC> struct RowWalk {
 // q - (K - 1 - s) on, and the stored rows have q >= K, so stage s's rows
 // 0 .. s feed nothing that is stored.  Beat m computes stage s's row
 // m - s - 1, so stage s first matters at beat 2s + 2: ACTIVE = m / 2.
-template <typename T, int K, int PH, int BC, int ACTIVE = K, class P>
+template <typename T, int K, int PH, int BC, int ACTIVE = K, bool CHECK = true, class P>
 __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec<T>::N> (&W)[3][K],
                                               const RowRing<T> &ring, RowWalk<BC> &walk, int nn, int nm,
                                               int lc, bool rev, const T *__restrict__ u,
                                               const T *__restrict__ v, P &pol) {
     constexpr int V = Vec<T>::N;
-    if (m >= total) return;
+    if (CHECK && m >= total) return;
     // The slot written here was read in the previous beat, whose stage
     // computations (issued before this point) consumed that value.
     static_assert(kRing == 3, "slots follow the 3-beat phase: row m sits in slot m % 3 == PH");
-    if (m + kRing - 1 < total) {
+    if (!CHECK || m + kRing - 1 < total) {
         ring_issue_at(ring, (PH + kRing - 1) % kRing, walk.g, nm, lc, u, v);
         walk.next(nn);
         pol.issue(m + kRing - 1);
@@ -206,7 +213,10 @@ __device__ __forceinline__ void pipeline_beat(int m, int total, Slice<CT<T>, Vec
             W[(PH + 2) % 3][s] = cur;  // stage s - 1's row, needed from the next beat on
         }
     }
-    if constexpr (ACTIVE == K) pol.finish(m - K, cur);
+    if constexpr (ACTIVE == K) {
+        if constexpr (CHECK) pol.finish(m - K, cur);
+        else pol.finish_main(m - K, cur);
+    }
 }
 
 // The first 2K beats of a strip (ACTIVE = M / 2), unrolled at compile time.
@@ -290,11 +300,17 @@ __device__ __forceinline__ void pipeline_strip(const StripGeom &geo, const T *__
     constexpr int M0 = P::kLightCone ? 2 * K : 0;
     if constexpr (P::kLightCone)
         pipeline_fill<T, K, BC, 0>(geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
-    for (int m = M0; m < geo.total; m += 3) {
-        pipeline_beat<T, K, M0 % 3>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
-        pipeline_beat<T, K, (M0 + 1) % 3>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
-        pipeline_beat<T, K, (M0 + 2) % 3>(m + 2, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+    int m = M0;
+    for (; m + 2 < geo.total; m += 3) {  // whole triplets: no per-beat bounds tests
+        pipeline_beat<T, K, M0 % 3, BC, K, false>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+        pipeline_beat<T, K, (M0 + 1) % 3, BC, K, false>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v,
+                                                         pol);
+        pipeline_beat<T, K, (M0 + 2) % 3, BC, K, false>(m + 2, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v,
+                                                         pol);
     }
+    // the last 0 .. 2 beats
+    pipeline_beat<T, K, M0 % 3>(m, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
+    pipeline_beat<T, K, (M0 + 1) % 3>(m + 1, geo.total, W, ring, walk, nn, nm, geo.lc, geo.rev, u, v, pol);
     cp_async_wait<0>();
 }
 
@@ -323,6 +339,13 @@ struct ForwardPolicy {
                 store_vec<T>(un + off, out.u);
                 store_vec<T>(vn + off, out.v);
             }
+        }
+    }
+    __device__ __forceinline__ void finish_main(int q, const Slice<CT<T>, Vec<T>::N> &out) {
+        const int64_t off = (int64_t)(geo.r0 + q - K) * nm + geo.sc;
+        if (geo.st_lane) {
+            store_vec<T>(un + off, out.u);
+            store_vec<T>(vn + off, out.v);
         }
     }
 };
@@ -356,6 +379,7 @@ struct ForwardAllPolicy {
         }
     }
     __device__ __forceinline__ void finish(int, const Slice<CT<T>, Vec<T>::N> &) {}
+    __device__ __forceinline__ void finish_main(int, const Slice<CT<T>, Vec<T>::N> &) {}
 };
 
 // H = halo lanes per side; any H >= ceil(K/V) is correct (a larger H than
