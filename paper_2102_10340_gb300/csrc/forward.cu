@@ -45,7 +45,10 @@ namespace rdk {
 
 namespace {
 
-constexpr int kStep1Block = 128;  // 72 registers: 7 blocks = 28 warps per SM (256: 24 warps, -2.5 %)
+// 72 registers.  4096^2 FP32, 400 back-to-back launches (Gcell-updates/s; 2 / 4 / 8 rows per warp):
+// 32 threads 245 / 389 / 372, 64 threads 398 / 392 / 364, 128 threads 393 / 393 / 362,
+// 256 threads 369 / 385 / 345.
+constexpr int kStep1Block = 64;
 
 // --------------------------------------------------------------------------- single step
 
@@ -382,7 +385,7 @@ int default_k(int dtype, int64_t nn, int64_t nm) {
 // 507 / 570 / 627 / 672 / 574 Gcell/s).
 int default_rows_step1(int dtype, int64_t nn, int64_t nm) {
     (void)nn; (void)nm;
-    return is_16bit(dtype) ? 32 : 4;
+    return is_16bit(dtype) ? 32 : dtype == RDCNN_F32 ? 2 : 4;
 }
 
 }  // namespace rdk

@@ -258,7 +258,7 @@ def test_plan_resolves_without_running(lib, L):
     var = ctypes.c_int(L.VARIANT_STEP1)
     tune = L.Tune(0, 0)
     assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == 0
-    assert (var.value, tune.k, tune.rows) == (L.VARIANT_STEP1, 1, 4)
+    assert (var.value, tune.k, tune.rows) == (L.VARIANT_STEP1, 1, 2)  # FP32 single step: 2-row strips
     assert lib.rdcnn_set_tune(h, ctypes.byref(L.Tune(0, 16))) == 0
     tune = L.Tune(0, 0)
     assert lib.rdcnn_plan(h, ctypes.byref(var), ctypes.byref(tune)) == 0 and tune.rows == 16

@@ -133,7 +133,7 @@ def test_plan_reports_the_launch_shape_that_runs(rd):
     g = rd.Grid(1024, 1024, None, dtype=F32)
     plan = g.plan("auto")
     assert plan["variant"] == "temporal" and 1 <= plan["k"] <= 8 and plan["rows"] >= 1
-    assert g.plan("step1") == {"variant": "step1", "k": 1, "rows": 4}  # FP32
+    assert g.plan("step1") == {"variant": "step1", "k": 1, "rows": 2}  # FP32: 2-row strips
     x = torch.from_numpy(f32(inp.uniform_field(70, 1024, 1024))).cuda().float()
     g.set_state(x, -x)
     g.run(3 * plan["k"] + 1)
