@@ -516,6 +516,16 @@ def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
     t_all = time.perf_counter() - t0
     all_bytes = ws1.numel()
     del ws1
+    # every state a checkpoint: the adjoint's own forward sweep stores all T states (4 GiB here)
+    # and the reverse sweep reads them, rebuilding nothing
+    wsT = torch.empty(g.adjoint_workspace_bytes(T, T), dtype=torch.uint8, device="cuda")
+    g.adjoint(T, x, x, gu, gv, T, workspace=wsT)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.adjoint(T, x, x, gu, gv, T, workspace=wsT)
+    t_every = time.perf_counter() - t0
+    every_bytes = wsT.numel()
+    del wsT
     g.set_state(x, x).run(T)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -554,6 +564,8 @@ def measure_adjoint(rd, torch, N=512, T=2000, quick=False):
             "value": N * N * T / t_adj / 1e9, "unit": "Gcell-updates/s (forward steps differentiated)",
             "all_states": {"checkpoints": 1, "adjoint_ms": t_all * 1e3, "adjoint_over_fwd": t_all / t_fwd,
                            "workspace_bytes": int(all_bytes)},
+            "every_state": {"checkpoints": T, "adjoint_ms": t_every * 1e3, "adjoint_over_fwd": t_every / t_fwd,
+                            "workspace_bytes": int(every_bytes)},
             "tape": {"sqrt": tape_sqrt, "all": tape_all,
                      "note": "backward_ms: rdcnn_adjoint_tape after a recording forward (rdcnn_run_record) "
                              "of the same T; adjoint_ms above includes its own forward sweep"},
@@ -834,7 +846,8 @@ def followon_summary(line):
     if a:
         out["adjoint"] = {"ms": a["adjoint_ms"], "plain_fwd_ms": a["plain_fwd_ms"],
                           "adjoint_over_fwd": a["adjoint_over_fwd"],
-                          "all_states_over_fwd": a["all_states"]["adjoint_over_fwd"]}
+                          "all_states_over_fwd": a["all_states"]["adjoint_over_fwd"],
+                          "every_state_over_fwd": a["every_state"]["adjoint_over_fwd"]}
         if "tape" in a:
             for key in ("sqrt", "all"):
                 t = a["tape"][key]
