@@ -83,3 +83,39 @@ def test_reference_arm_prints_contract_line(monkeypatch, capsys):
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_followon_summary_ends_the_line_and_carries_the_ratios():
+    """The JSON line ends with a compact `followon` object that repeats the companion figures
+    (single step, batched and adjoint ratios, gradient errors), so that a reader of the line's
+    tail sees them; built here from a hand-made line (no GPU)."""
+    import json
+
+    import bench
+
+    line = {"value": 1450.0, "roofline": {"frac": 0.49},
+            "single_step_kernel": {"gcell_s": 392.0, "frac": 0.94},
+            "batched": {"value": 1330.0, "plain_fwd_value": 260.0, "vs_plain_fwd": 5.1},
+            "adjoint": {"adjoint_ms": 10.8, "plain_fwd_ms": 2.9, "adjoint_over_fwd": 3.7,
+                        "all_states": {"adjoint_over_fwd": 2.9}, "every_state": {"adjoint_over_fwd": 2.7},
+                        "tape": {"sqrt": {"record_over_fwd": 1.0, "backward_over_fwd": 2.7},
+                                 "all": {"record_over_fwd": 0.95, "backward_over_fwd": 1.8}},
+                        "gradient_check": {
+                            "short_horizon": {"T": 100,
+                                              "fp32": {"dLdu0_dir_rel_err": 3e-4, "dLdv0_dir_rel_err": 1e-5,
+                                                       "gene_rel_err": 3e-7},
+                                              "fp64": {"dLdu0_dir_rel_err": 8e-7, "dLdv0_dir_rel_err": 3e-8,
+                                                       "gene_rel_err": 9e-9}},
+                            "workload_horizon": {"T": 2000,
+                                                 "fp32": {"gene_rel_err": 3e-6, "dLdu0_vs_fp64_adjoint": 4e-3},
+                                                 "fp64": {"gene_rel_err": 4e-6}}}}}
+    line["followon"] = bench.followon_summary(line)
+    text = json.dumps(line)
+    tail = text[text.rindex('"followon"'):]
+    assert list(json.loads(text))[-1] == "followon"
+    f = json.loads(text)["followon"]
+    assert f["batched"]["vs_plain_fwd"] == 5.1 and f["single_step"]["frac_hbm"] == 0.94
+    assert f["adjoint"]["tape_sqrt"]["backward_over_fwd"] == 2.7 and f["adjoint"]["tape_all"]["backward_over_fwd"] == 1.8
+    assert f["adjoint"]["grad_err_fp64"]["T100_dLdu0_dir_rel_err"] == 8e-7
+    assert f["adjoint"]["grad_err_fp32"]["T2000_dLdu0_vs_fp64"] == 4e-3
+    assert len(tail) < 1500  # small enough to survive a truncated log tail
