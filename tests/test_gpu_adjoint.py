@@ -417,3 +417,29 @@ def test_adjoint_tape_full_size_f32(rd, oracle_mod):
     a = np.array([gp[k] for k in NAMES])
     b = np.array([rp[k] for k in NAMES])
     assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("T", [0, 1, 2, 3, 9])
+@pytest.mark.parametrize("nck", [0, 1, 100], ids=["sqrtT", "one", "all"])
+def test_tape_short_horizons(rd, T, nck):
+    """Horizons of 0 .. 9 steps through the recorded forward and the tape adjoint: the same
+    bits as rdcnn_run and rdcnn_adjoint (T = 0 leaves the state and passes the co-state
+    through with a zero gene gradient)."""
+    nn, nm = 16, 32
+    x = inp.uniform_field(81, nn, nm)
+    y = inp.uniform_field(82, nn, nm)
+    wu = inp.uniform_field(83, nn, nm)
+    wv = inp.uniform_field(84, nn, nm)
+    params = inp.default_params(Du=0.11, Dv=0.37)
+    g = rd.Grid(nn, nm, params, dtype=F64)
+    g.set_state(_dev(x, F64), _dev(y, F64))
+    tape = g.run_record(T, nck)
+    ru, rv = gpu_run(rd, x, y, params, T, F64)
+    assert np.array_equal(g.u.cpu().numpy(), ru) and np.array_equal(g.v.cpu().numpy(), rv)
+    du, dv, gp = g.adjoint_tape(T, tape, _dev(wu, F64), _dev(wv, F64), nck)
+    eu, ev, ep = g.adjoint(T, _dev(x, F64), _dev(y, F64), _dev(wu, F64), _dev(wv, F64), nck)
+    torch.cuda.synchronize()
+    assert torch.equal(du, eu) and torch.equal(dv, ev)
+    assert all(gp[k] == ep[k] for k in NAMES)
+    if T == 0:
+        assert np.array_equal(du.cpu().numpy(), wu) and all(gp[k] == 0.0 for k in NAMES)
