@@ -18,8 +18,9 @@ GRID_CANDIDATES_F32 = [("temporal", k, r) for k in (2, 3, 4, 5, 6, 8) for r in (
 GRID_CANDIDATES_F64 = [("temporal", k, r) for k in (2, 3, 4) for r in (0, 32, 64, 128)] + \
                       [("temporal2", k, r) for k in (2, 4) for r in (0, 64)] + \
                       [("step1", 1, r) for r in (4, 8, 16)]
-# 256-row strips won at the 256-instance sweep (k = 4: 1156 against 1130 Gcell/s at 128 rows)
-BATCH_CANDIDATES = [(k, r) for k in (2, 3, 4, 6, 8) for r in (16, 32, 64, 128, 256, 512)]
+# 256-row strips won at the 256-instance sweep with four-warp blocks (k = 4: 1156 against 1130
+# Gcell/s at 128 rows), 128-row strips with one-warp blocks (1298); 96 and 192 lie between
+BATCH_CANDIDATES = [(k, r) for k in (2, 3, 4, 6, 8) for r in (16, 32, 64, 96, 128, 192, 256, 512)]
 
 
 def _time(fn, reps: int = 2) -> float:
