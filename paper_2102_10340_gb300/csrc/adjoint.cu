@@ -365,8 +365,7 @@ int adjoint_t(rdcnn_t *h, int64_t nn, int64_t nm, const rdcnn_params &p, int dty
 }
 
 // Shared checks of the adjoint entry points.
-int adjoint_checks(const rdcnn_t *h, int64_t T, int dtype, int64_t nm) {
-    (void)h;
+int adjoint_checks(int64_t T, int dtype, int64_t nm) {
     if (is_16bit(dtype)) return set_error(RDCNN_EINVAL, "the adjoint supports FP32 / FP64 handles only");
     if (T < 0) return set_error(RDCNN_EINVAL, "T must be >= 0");
     const int V = vec_width(dtype);
@@ -400,7 +399,7 @@ int rdcnn_adjoint(rdcnn_t *h, int64_t T, const void *u0, const void *v0, const v
     int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
-    rc = adjoint_checks(h, T, dtype, nm);
+    rc = adjoint_checks(T, dtype, nm);
     if (rc < 0) return rc;
     if (!u0 || !v0 || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
         return set_error(RDCNN_EINVAL, "NULL argument");
@@ -436,7 +435,7 @@ int rdcnn_run_record(rdcnn_t *h, int64_t T, int64_t n_checkpoints, void *tape, s
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
     if (!h->bound) return set_error(RDCNN_ESTATE, "handle is not bound");
-    rc = adjoint_checks(h, T, dtype, nm);
+    rc = adjoint_checks(T, dtype, nm);
     if (rc < 0) return rc;
     if (!tape) return set_error(RDCNN_EINVAL, "tape is NULL");
     if (!aligned16(tape) || !aligned16(h->u) || !aligned16(h->v) || !aligned16(h->ws))
@@ -463,7 +462,7 @@ int rdcnn_adjoint_tape(rdcnn_t *h, int64_t T, int64_t n_checkpoints, const void 
     int64_t nn, nm; rdcnn_params p; int dtype, reaction, boundary; cudaStream_t s;
     int rc = handle_view(h, &nn, &nm, &p, &dtype, &reaction, &s, &boundary);
     if (rc < 0) return rc;
-    rc = adjoint_checks(h, T, dtype, nm);
+    rc = adjoint_checks(T, dtype, nm);
     if (rc < 0) return rc;
     if (!tape || !dLdu_T || !dLdv_T || !dLdu0 || !dLdv0 || !grad || !workspace)
         return set_error(RDCNN_EINVAL, "NULL argument");
