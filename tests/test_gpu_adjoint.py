@@ -97,7 +97,8 @@ def test_f32_checkerboard_mse_512(rd, oracle_mod, T, gtol):
     State gradient: the FP32 forward trajectory differs from the FP64 one by rounding, and
     dL/du0 is sensitive to it: an FP64 co-state swept along the FP32 trajectory is already
     ~2e-3 away from the FP64 reference, while the FP32 co-state arithmetic itself adds ~1e-7
-    (measured on the CPU).  The bound below is therefore 1e-2 normwise."""
+    (measured on the CPU); the GPU measured 2.4e-3 / 2.5e-3 (u0 / v0) at T = 200 and
+    3.6e-3 / 3.9e-3 at T = 2000.  The bound below is therefore 5e-3 normwise."""
     N = 512
     params = inp.default_params()
     x = f32(inp.uniform_field(0, N, N))
@@ -107,7 +108,7 @@ def test_f32_checkerboard_mse_512(rd, oracle_mod, T, gtol):
     du, dv, g = _gpu_adjoint(rd, x, x, params, T, gu, 0 * gu, F32)
     ou, ov, og = oracle_mod.adjoint(x, x, params, T, gu, 0 * gu, nthreads=cpu_threads())
     assert np.linalg.norm(g - og) <= gtol * np.linalg.norm(og), dict(zip(NAMES, np.abs(g - og)))
-    assert normwise(du, ou) <= 1e-2 and normwise(dv, ov) <= 1e-2
+    assert normwise(du, ou) <= 5e-3 and normwise(dv, ov) <= 5e-3
 
 
 def test_f32_adjoint_short_horizon_is_tight(rd, oracle_mod):
