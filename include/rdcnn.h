@@ -305,7 +305,7 @@ int rdcnn_adjoint_workspace_bytes(const rdcnn_t *h, int64_t T, int64_t n_checkpo
  * and the co-state dL/du_T, dL/dv_T of a loss L of the final state, writes
  * dL/du0, dL/dv0 (device planes) and grad[6] = dL/d{Du, Dv, a, b, eps, c}
  * (host array, FP64).  Forward states are rebuilt from n_checkpoints stored
- * states (0 = ceil(sqrt(T)); n_checkpoints >= T stores every state, T planes
+ * states (0 = ceil(sqrt(T)); n_checkpoints >= T stores every state, T plane
  * pairs of workspace, and rebuilds nothing).  All planes are device planes of the handle's
  * size and dtype; the bound u/v/workspace of the handle are not touched.
  * The handle's boundary applies (the zero-flux Laplacian, like the periodic
