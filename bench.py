@@ -619,6 +619,8 @@ def adjoint_gradient_check(rd, torch, N=512, T=2000, quick=False):
             out.append(central(f, step))
         return np.array(out)
 
+    adjoint_ms = {}
+
     def adjoints(steps):
         res = {}
         for tag, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
@@ -626,7 +628,10 @@ def adjoint_gradient_check(rd, torch, N=512, T=2000, quick=False):
             xs = x.to(dt)
             g.set_state(xs, xs).run(steps)
             gu = (2.0 * (g.u.double() - tgt) / g.u.numel()).to(dt).contiguous()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             du0, dv0, gp = g.adjoint(steps, xs, xs, gu, torch.zeros_like(gu))
+            adjoint_ms[f"{tag}_T{steps}"] = (time.perf_counter() - t0) * 1e3  # first call: includes set-up
             res[tag] = (du0.double(), dv0.double(), np.array([gp[k] for k in rd.GRAD_NAMES]))
             g.close()
         return res
@@ -652,6 +657,7 @@ def adjoint_gradient_check(rd, torch, N=512, T=2000, quick=False):
                       "gene_rel_err": float(np.linalg.norm(a_g - fdg) / np.linalg.norm(fdg))}
     out["short_horizon"] = short
     if quick:
+        out["adjoint_ms_first_call"] = adjoint_ms
         return out
     # the workload's horizon: gene entries against differences, state against the FP64 adjoint
     fdg = gene_fd(T)
@@ -667,6 +673,7 @@ def adjoint_gradient_check(rd, torch, N=512, T=2000, quick=False):
     full["state_fd_unresolved"] = {"h_1e-5": central(fu, 1e-5), "h_1e-4": central(fu, 1e-4),
                                    "adjoint_fp64": float(torch.sum(su * du))}
     out["workload_horizon"] = full
+    out["adjoint_ms_first_call"] = adjoint_ms
     g64.close()
     return out
 
